@@ -1,0 +1,371 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Every check here compares the oracle with a closed form, an invariant, an
+independent method (discrete-ordinates transport for the 1D slab), brute
+force from independently regenerated random numbers, published known-answer
+vectors, or printed values of arXiv 2604.13929.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import philox_ref
+from oracle import oracle as orc
+from paper_2604_13929_gb300 import inputs
+from rte_slab import SlabSolution
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+Q32 = 2.0 ** 32
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [line.split() for line in f if line.strip() and not line.startswith("#")]
+
+
+# ------------------------------------------------------------------ RNG ---
+
+def test_philox_known_answers():
+    for row in _rows("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        assert orc.philox4x32_10(v[0:4], v[4:6]) == tuple(v[6:10])
+        ref = philox_ref.philox4x32_10(*[np.array([x]) for x in v[0:4]], v[4], v[5])
+        assert tuple(int(r[0]) for r in ref) == tuple(v[6:10])
+
+
+def test_philox_matches_second_implementation():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        c = [int(x) for x in rng.integers(0, 2 ** 32, 4)]
+        k = [int(x) for x in rng.integers(0, 2 ** 32, 2)]
+        ref = philox_ref.philox4x32_10(*[np.array([x]) for x in c], k[0], k[1])
+        assert orc.philox4x32_10(c, k) == tuple(int(r[0]) for r in ref)
+
+
+def test_philox_stream_statistics():
+    """Chi^2 of the uniforms per word, bit balance, and no correlation
+    between consecutive photon ids or between words of one block."""
+    pids = np.arange(1 << 16, dtype=np.uint64)
+    words = philox_ref.event_words(pids, 3, 20260809)
+    for w in words:
+        u = philox_ref.uniform(w)
+        h, _ = np.histogram(u, bins=64, range=(0, 1))
+        e = u.size / 64
+        chi2 = float(((h - e) ** 2 / e).sum())
+        assert chi2 < 63 + 6 * math.sqrt(2 * 63)       # ~ 6 sigma
+        bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(axis=0)
+        assert np.all(np.abs(bits - 0.5) < 6 * 0.5 / math.sqrt(u.size))
+    u = [philox_ref.uniform(w) - 0.5 for w in words]
+    lim = 6 / math.sqrt(pids.size) / 12
+    assert abs(float(np.mean(u[0][1:] * u[0][:-1]))) < lim
+    for a in range(4):
+        for b in range(a + 1, 4):
+            assert abs(float(np.mean(u[a] * u[b]))) < lim
+
+
+def test_uniform_mapping_open_interval_and_float32_exact():
+    for r in (0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFFFF, 0x80000000):
+        u = orc.uniform(r)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+        assert u == ((r >> 9) * 2 + 1) / 2 ** 24
+    assert orc.uniform(0) == 2.0 ** -24
+    assert orc.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+
+
+# ------------------------------------------------------- phase function ---
+
+@pytest.mark.parametrize("g", [0.0, 0.3, 0.7, 0.9, -0.5])
+def test_hg_inverse_cdf_against_analytic_cdf(g):
+    """F_HG(hg_cos(u)) = u with the closed-form HG cumulative distribution."""
+    for u in np.linspace(1e-6, 1 - 1e-6, 257):
+        c = orc.hg_cos(u, g)
+        if abs(g) < 1e-6:
+            F = 0.5 * (c + 1.0)
+        else:
+            F = (1 - g * g) / (2 * g) * (1 / math.sqrt(1 + g * g - 2 * g * c) - 1 / (1 + g))
+        assert abs(F - u) < 1e-12
+
+
+@pytest.mark.parametrize("g", [0.0, 0.3, 0.7, 0.9, -0.5])
+def test_hg_moments_equal_powers_of_g(g):
+    """<cos> = g and <P2(cos)> = g^2 (HG Legendre moments), midpoint rule in u."""
+    n = 200000
+    u = (np.arange(n) + 0.5) / n
+    c = np.array([orc.hg_cos(x, g) for x in u[::10]])   # 20000 nodes
+    c_all = np.interp(u, u[::10], c)
+    m1 = float(c_all.mean())
+    m2 = float((1.5 * c_all ** 2 - 0.5).mean())
+    assert abs(m1 - g) < 2e-4
+    assert abs(m2 - g * g) < 2e-4
+
+
+def test_hg_sampled_mean_cosine_equals_g():
+    """The HG mean cosine over Philox uniforms equals g within 4 SE."""
+    g = 0.7
+    w = philox_ref.event_words(np.arange(100000), 1, 99)[0]
+    c = np.array([orc.hg_cos(u, g) for u in philox_ref.uniform(w)])
+    assert abs(c.mean() - g) < 4 * c.std() / math.sqrt(c.size)
+
+
+def test_rotation_preserves_angle_and_norm():
+    rng = np.random.default_rng(1)
+    dirs = rng.normal(size=(300, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    dirs = np.vstack([dirs, [[0, 0, 1.0], [0, 0, -1.0], [1e-4, 0, math.sqrt(1 - 1e-8)]]])
+    for d in dirs:
+        cost = rng.uniform(-1, 1)
+        phi = rng.uniform(0, 2 * math.pi)
+        v = orc.rotate(d, cost, phi)
+        assert abs(np.linalg.norm(v) - 1) < 1e-14
+        # above |uz| = 0.99999 the rotation treats d as exactly +-z, which
+        # moves the polar angle by at most arccos(0.99999) ~ 4.5e-3 rad
+        tol = 5e-3 if abs(d[2]) > 0.99999 else 1e-9
+        assert abs(float(np.dot(v, d)) - cost) < tol
+
+
+def test_rotation_azimuth_is_uniform_about_old_direction():
+    """Averaging over a uniform azimuth leaves only cos(theta) times d."""
+    rng = np.random.default_rng(2)
+    for d in [np.array([0.3, -0.5, 0.81]), np.array([0, 0, 1.0]), np.array([0.6, 0.8, 0.0])]:
+        d = d / np.linalg.norm(d)
+        cost = 0.4
+        phis = (np.arange(720) + 0.5) * 2 * math.pi / 720
+        m = np.mean([orc.rotate(d, cost, p) for p in phis], axis=0)
+        assert np.allclose(m, cost * d, atol=1e-12)
+    v = orc.rotate([0, 0, 1.0], 0.0, 0.0)
+    assert np.allclose(v, [1, 0, 0], atol=1e-15)
+
+
+# ------------------------------------------------------ closed forms -----
+
+def test_pure_absorption_slab_transmits_exp_minus_mua_L():
+    """mu_s = 0, all solid: T = exp(-mu_a L) exactly, R = 0, A = 1 - T,
+    and the layer fluence is exp(-mu_a z)(1 - exp(-mu_a))/mu_a."""
+    nz, mua = 20, 0.05
+    res = orc.run(inputs.all_solid(nz, 3, 5), 0.0, mua, 0.7, 5000, 3)
+    n = orc.normalise(res)
+    assert abs(n["T"] - math.exp(-mua * nz)) < 1e-9
+    assert n["R"] == 0.0 and n["gated"] == 0.0 and n["lost"] == 0.0
+    assert abs(n["A"] - (1 - math.exp(-mua * nz))) < 1e-9
+    layer = n["fluence"].reshape(nz, -1).mean(axis=1)
+    z = np.arange(nz)
+    expect = np.exp(-mua * z) * (1 - math.exp(-mua)) / mua
+    assert np.allclose(layer, expect, rtol=1e-9, atol=0)
+    assert res["counts"]["steps"] == 5000 * nz
+
+
+def test_all_pore_mask_gives_unit_transmission_and_fluence():
+    nz = 24
+    res = orc.run(inputs.all_pore(nz, 4, 6), 0.5, 0.005, 0.7, 4000, 11)
+    n = orc.normalise(res)
+    assert n["T"] == 1.0 and n["R"] == 0.0 and n["A"] == 0.0
+    # every photon leaves exactly q32(1) of track in every layer
+    assert all(orc.exact_sum(res["field"][z]) == 4000 * 2 ** 32 for z in range(nz))
+    assert np.all(n["depth"][1][(np.arange(nz) * 64) // nz] == 1.0)
+    assert n["pore_path_mean"] == nz
+    h = res["hist"]
+    assert h[64] == 4000 * 2 ** 32 and h.sum() == h[64]
+    assert res["counts"]["interactions"] == 0
+
+
+def test_depth_bins_with_ragged_nz():
+    """nz not a multiple of 64: b = floor(iz*64/nz); all-pore means are 1."""
+    nz = 100
+    res = orc.run(inputs.all_pore(nz, 2, 3), 0.5, 0.005, 0.7, 500, 1)
+    n = orc.normalise(res)
+    assert np.all(n["depth_count"][0] == 0)
+    assert np.all(n["depth"][1] == 1.0)
+    assert n["depth_count"][1].sum() == nz * 6
+    bins = (np.arange(nz) * 64) // nz
+    assert np.array_equal(np.bincount(bins, minlength=64) * 6, n["depth_count"][1])
+
+
+def test_path_cap_truncates_and_gates_weight():
+    nz = 64
+    res = orc.run(inputs.all_pore(nz, 2, 2), 0.5, 0.005, 0.7, 1000, 5, s_max=32.5)
+    n = orc.normalise(res)
+    assert n["gated"] == 1.0 and n["T"] == 0.0 and n["closure"] == 1.0
+    layer = [orc.exact_sum(res["field"][z]) for z in range(nz)]
+    assert all(v == 1000 * 2 ** 32 for v in layer[:32])
+    assert layer[32] == 1000 * 2 ** 31 and all(v == 0 for v in layer[33:])
+
+
+def test_default_path_cap_reproduces_printed_time_gates():
+    """Eq. tend as a path cap reproduces the paper's printed t_end values."""
+    c, n_eff, h, nz = 299792458.0, 1.746, 1.45e-6, 384
+    for row in _rows("paper_time_gate.txt"):
+        phi, t_end = float(row[0]), float(row[1])
+        s = orc.default_path_cap(nz, phi, 20118 * h, 5159 * h, 0.0)
+        t = s * h / (c / n_eff)
+        assert abs(t / t_end - 1) < 2e-3
+
+
+# ---------------------------------------- brute force without scattering --
+
+def test_pure_absorption_through_mask_brute_force():
+    """mu_s = 0 through a random mask: every photon runs straight down its
+    column, so its transmitted weight and every voxel deposit follow from the
+    column's solid count.  Launch columns are re-derived with the separate
+    Philox implementation (catches axis transposition and phase mix-ups)."""
+    nz, ny, nx, mua, seed, N = 10, 7, 5, 0.08, 77, 3000
+    mask = inputs.random_mask((nz, ny, nx), 0.6, 4)
+    res = orc.run(mask, 0.0, mua, 0.0, N, seed)
+    w0 = philox_ref.event_words(np.arange(N), 0, seed)
+    ix = np.floor(philox_ref.uniform(w0[0]) * nx).astype(int)
+    iy = np.floor(philox_ref.uniform(w0[1]) * ny).astype(int)
+    field = np.zeros((nz, ny, nx))
+    T = 0.0
+    e1 = math.exp(-mua)
+    for x, y in zip(ix, iy):
+        w = 1.0
+        for z in range(nz):
+            if mask[z, y, x]:
+                field[z, y, x] += w
+            else:
+                field[z, y, x] += w * (1 - e1) / mua
+                w *= e1
+        T += w
+    n = orc.normalise(res)
+    assert abs(n["T"] - T / N) < 1e-9
+    assert np.allclose(res["field"].astype(np.float64) / Q32, field, rtol=1e-9, atol=N * 2.0 ** -32)
+    assert n["R"] == 0.0
+
+
+# -------------------------------------------------- invariances -----------
+
+def test_optical_depth_is_carried_across_pores():
+    """Void layers in a laterally uniform medium change neither the direction
+    nor the optical depth: a layered mask and the compacted solid slab give
+    the same per-photon events, exit weights and absorbed weights."""
+    pattern = [1, 0, 0, 1, 1, 0, 1, 0, 0, 0, 1, 0, 1, 1]
+    n_solid = pattern.count(0)
+    kw = dict(mus=0.6, mua=0.03, g=0.7, n_photons=3000, seed=21, n_rec=3000, s_max=1e9)
+    a = orc.run(inputs.layered(pattern, 3, 3), **kw)
+    b = orc.run(inputs.all_solid(n_solid, 3, 3), **kw)
+    ia, ib = a["rec_ints"], b["rec_ints"]
+    assert np.array_equal(ia[:, 0], ib[:, 0])      # interaction events
+    assert np.array_equal(ia[:, 2], ib[:, 2])      # exit kind
+    assert np.array_equal(ia[:, 3], ib[:, 3])      # roulette survivals
+    assert np.allclose(a["rec_vals"][:, 0], b["rec_vals"][:, 0], rtol=1e-9, atol=1e-15)
+    assert np.allclose(a["rec_vals"][:, 3], b["rec_vals"][:, 3], rtol=1e-9, atol=1e-15)
+    na, nb = orc.normalise(a), orc.normalise(b)
+    for k in ("R", "T", "A"):
+        assert abs(na[k] - nb[k]) < 1e-9
+
+
+def test_lateral_periodicity_makes_slab_independent_of_width():
+    """A laterally uniform slab is the same problem for any periodic width."""
+    kw = dict(mus=0.5, mua=0.02, g=0.6, n_photons=2000, seed=8, n_rec=2000)
+    a = orc.run(inputs.all_solid(9, 1, 1), **kw)
+    b = orc.run(inputs.all_solid(9, 6, 5), **kw)
+    assert np.array_equal(a["rec_ints"][:, [0, 2, 3]], b["rec_ints"][:, [0, 2, 3]])
+    assert np.allclose(a["rec_vals"][:, [0, 2, 3]], b["rec_vals"][:, [0, 2, 3]], rtol=1e-9)
+    za, zb = a["rec_sites"][:, :, 2], b["rec_sites"][:, :, 2]
+    assert np.allclose(za, zb, atol=1e-9)
+
+
+def test_lateral_transport_is_isotropic():
+    """Between the 1st and 8th interaction sites the mean lateral
+    displacement is zero and x, y spread alike (uniform azimuth)."""
+    res = orc.run(inputs.all_solid(400, 3, 3), 1.0, 0.001, 0.6, 20000, 31, n_rec=20000,
+                  s_max=1e9)
+    ok = res["rec_ints"][:, 0] >= 8
+    d = res["rec_sites"][ok, 7, :] - res["rec_sites"][ok, 0, :]
+    assert ok.sum() > 10000
+    for a in (0, 1):
+        assert abs(d[:, a].mean()) < 4 * d[:, a].std() / math.sqrt(ok.sum())
+    vx, vy = d[:, 0].var(), d[:, 1].var()
+    assert abs(vx / vy - 1) < 4 * math.sqrt(4.0 / ok.sum())
+
+
+def test_thread_count_does_not_change_integer_tallies(spinodal32_90):
+    kw = dict(mus=0.5, mua=0.005, g=0.7, n_photons=3000, seed=3)
+    a = orc.run(spinodal32_90, n_threads=1, **kw)
+    b = orc.run(spinodal32_90, n_threads=4, **kw)
+    for k in ("R", "T", "A", "gated", "lost", "gain", "depth", "hist", "field"):
+        assert np.array_equal(a[k], b[k])
+    assert a["counts"] == b["counts"] and a["sum_wP"] == b["sum_wP"]
+
+
+def test_photon_id_ranges_compose(spinodal32_90):
+    kw = dict(mus=0.5, mua=0.005, g=0.7, seed=3)
+    a = orc.run(spinodal32_90, n_photons=2000, **kw)
+    b1 = orc.run(spinodal32_90, n_photons=700, **kw)
+    b2 = orc.run(spinodal32_90, n_photons=1300, pid_begin=700, **kw)
+    assert np.array_equal(a["field"], b1["field"] + b2["field"])
+    assert np.array_equal(a["R"], b1["R"] + b2["R"])
+
+
+# ----------------------------------------- independent transport solver --
+
+@pytest.mark.parametrize("mus,mua,g,nz", [(0.5, 0.05, 0.7, 12), (0.5, 0.05, 0.0, 12),
+                                          (0.8, 0.1, -0.3, 8)])
+def test_slab_matches_discrete_ordinates(mus, mua, g, nz):
+    """Homogeneous slab: R, T, A and the layer fluence agree with the
+    discrete-ordinates solution of the same RTE within 4 SE (+ its own
+    angular-discretisation allowance)."""
+    with np.errstate(over="ignore"):
+        sol = SlabSolution(mus, mua, g, nz)
+        ref = {"R": sol.reflectance(), "T": sol.transmittance(), "A": sol.absorptance()}
+        prof = sol.layer_means(nz)
+    res = orc.run(inputs.all_solid(nz, 2, 2), mus, mua, g, 600000, 1234)
+    n = orc.normalise(res)
+    for k in ("R", "T", "A"):
+        assert abs(n[k] - ref[k]) < 4 * n[k + "_se"] + 1e-4, k
+    nb = orc.NBATCH
+    per = (res["depth"][:, 0, :].astype(np.float64) / Q32 * 4 / res["photons"][:, None])
+    bins = (np.arange(nz) * 64) // nz
+    mc = n["depth"][0][bins]
+    se = (per.std(axis=0, ddof=1) / math.sqrt(nb))[bins] / 4
+    assert np.all(np.abs(mc - prof) < 4 * se + 1e-4 * prof)
+
+
+# ----------------------------------------------------- budget & estimators --
+
+def test_closure_and_absorption_estimator(spinodal64):
+    res = orc.run(spinodal64, 0.5, 0.005, 0.7, 20000, 20260809)
+    n = orc.normalise(res)
+    assert abs(n["closure"] - 1) < 1e-9
+    rta = (res["R"] + res["T"] + res["A"]).astype(np.float64) / Q32 / res["photons"]
+    assert abs(n["RTA"] - 1) < 4 * rta.std(ddof=1) / 4 + 1e-9
+    # absorbed weight equals mu_a times the solid track length
+    solid_track = orc.exact_sum(res["field"][spinodal64 == 0]) / Q32
+    A = orc.exact_sum(res["A"]) / Q32
+    assert abs(A - 0.005 * solid_track) < 1e-9 * max(A, 1) + 20000 * 2 ** -32 * 8
+    # field-derived phase sums equal the direct depth tallies exactly
+    fs = orc.field_phase_sums(res["field"], spinodal64)
+    for p in range(2):
+        for b in range(64):
+            assert fs[p, b] == orc.exact_sum(res["depth"][:, p, b])
+    # dilution identity on the tallies (Eq. dilution)
+    assert abs(n["identity_residual"]) < 1e-12
+
+
+def test_roulette_is_unbiased():
+    """Roulette on (threshold 0.05, survival 1/10) vs off: same R, T, A."""
+    mask = inputs.all_solid(10, 2, 2)
+    kw = dict(mus=2.0, mua=0.2, g=0.5, n_photons=200000, seed=17)
+    on = orc.normalise(orc.run(mask, rr_weight=0.05, **kw))
+    off = orc.normalise(orc.run(mask, rr_weight=0.0, **kw))
+    assert on["lost"] > 0 and off["lost"] == 0
+    for k in ("R", "T", "A"):
+        se = math.hypot(on[k + "_se"], off[k + "_se"])
+        assert abs(on[k] - off[k]) < 4 * se + 1e-6, k
+    assert abs(on["closure"] - 1) < 1e-9
+
+
+def test_printed_estimator_vectors():
+    """The oracle's estimator algebra reproduces the paper's printed
+    <Phi>_1D, r, concentration ratio and dilution prediction from its printed
+    <Phi>_3D, <Phi>_pore and porosity, to the printed precision."""
+    for row in _rows("paper_estimators.txt"):
+        phi, p3, p1, pp, r, ratio_m, ratio_p = map(float, row)
+        e = orc.phase_estimators(p3, pp, phi)
+        assert abs(e["phi_1d"] / p1 - 1) < 2e-3
+        assert abs(e["r"] / r - 1) < 2e-3
+        assert abs(e["ratio"] / ratio_m - 1) < 2e-3
+        # the prediction evaluated at the printed r
+        assert abs(orc.phase_estimators(1.0, r, phi)["predicted_ratio"] - ratio_p) < 3e-4
