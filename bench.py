@@ -1,0 +1,303 @@
+"""Benchmark: voxel Monte Carlo photon migration on the 256^3 spinodal mask.
+
+One step = one pass of the whole hot path over one batch: reset the tallies,
+transport 1e8 photons through the resident bit-packed mask (full Q32.32 voxel
+fluence tally), FP64 normalisation and estimators on the GPU, results to the
+host.  Workload: 256^3 Cahn-Hilliard spinodal mask (4000 steps, mask seed 0),
+porosity 0.90, solid mu_s h = 0.5, mu_a h = 0.005, HG g = 0.7, FP32 transport.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_VOX = 256
+POROSITY = 0.90
+CH_STEPS = 4000
+MUS, MUA, G = 0.5, 0.005, 0.7
+SEED = 20260809
+PHOTONS = 100_000_000
+METRIC = "photons/s & voxel-steps/s at 256³ φ=0.9"
+WORKLOAD = ("256^3 Cahn-Hilliard spinodal mask (dt 0.1, 4000 steps, seed 0), porosity 0.90; "
+            "solid mu_s h 0.5, mu_a h 0.005, HG g 0.7; pores void; periodic x/y; "
+            "1e8 photons per step; FP32 transport; Q32.32 voxel fluence field")
+# Algorithmic lane-operations per unit of work (derivation in the design notes):
+# a voxel step, an interaction event and a photon launch.
+OPS_STEP, OPS_INTERACT, OPS_LAUNCH = 30, 120, 90
+ISSUE_PER_SM_CLK = 4          # warp instructions per SM per clock (4 schedulers)
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons in the background."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            if len(r) >= 8:
+                for n, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_mask(device):
+    from paper_2604_13929_gb300 import inputs
+    return inputs.spinodal_mask(N_VOX, POROSITY, CH_STEPS, seed=0, device=device)
+
+
+def cpu_baseline(mask, target_s=15.0):
+    """The FP64 oracle, as it stands, on all host cores over a bounded sample."""
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = orc.run(mask, MUS, MUA, G, 2000, SEED, n_threads=cores, field=True)
+    dt = time.perf_counter() - t0
+    n = int(min(max(2000 * target_s / max(dt, 1e-3), 2000), 5_000_000))
+    t0 = time.perf_counter()
+    r = orc.run(mask, MUS, MUA, G, n, SEED, n_threads=cores, field=True)
+    dt = time.perf_counter() - t0
+    steps = r["counts"]["steps"]
+    return {"value": n / dt, "unit": "photons/s", "cores": cores, "kind": "oracle",
+            "sample": f"photon ids [0, {n}) of the same 256^3 phi=0.90 workload with the full "
+                      f"voxel field, {dt:.1f} s wall on {cores} threads",
+            "voxel_steps_per_s": steps / dt, "photons": n, "seconds": dt}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    from paper_2604_13929_gb300 import inputs
+    mask = make_mask(inputs.default_device())
+    per_step = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(mask, target_s=args.cpu_seconds)
+        if i >= args.warmup:
+            per_step.append(cb)
+        base = cb
+    value = statistics.median(c["value"] for c in per_step)
+    ms = statistics.median(c["seconds"] * 1e3 for c in per_step)
+    line = {"metric": METRIC, "value": value, "unit": "photons/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD.replace("1e8 photons per step",
+                                                    f"{base['photons']} photons per step")
+                       .replace("FP32 transport", "FP64 CPU oracle")},
+            "voxel_steps_per_s": statistics.median(c["voxel_steps_per_s"] for c in per_step),
+            "cpu_baseline": {"value": value, "unit": "photons/s", "cores": base["cores"],
+                             "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": value, "unit": "photons/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--photons", type=int, default=PHOTONS)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2604_13929_gb300 import build as spbuild
+    spbuild.build()
+    from paper_2604_13929_gb300 import spmc
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    mask = make_mask("cuda")
+    stream = torch.cuda.current_stream()
+    seed = SEED + rank                      # replicas: independent photon streams per rank
+    sim = spmc.Simulation(mask, MUS, MUA, G)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    def step(ev=None):
+        sim.reset(stream)
+        if ev is not None:
+            ev[0].record(stream)
+        sim.run(args.photons, seed, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        return sim.tallies(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    barrier()
+
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with Clocks(local_rank) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        start.record(stream)
+        for i in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.nvtx.range_push("spmc_step")
+            results.append(step(kev[i]))
+            torch.cuda.nvtx.range_pop()
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms_total = start.elapsed_time(stop)
+    kernel_ms = [a.elapsed_time(b) for a, b in kev]
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    last = results[-1]
+    steps_per_photon = last["steps"] / last["photons"]
+    photons_total = args.photons * args.steps * world
+    value = photons_total / (ms_total / 1e3)
+    clocks = clk.summary()
+
+    # roofline of the transport kernel: algorithmic lane-operations / issue peak
+    launch_ms = statistics.mean(kernel_ms)
+    ops = (OPS_STEP * last["steps"] + OPS_INTERACT * last["interactions"]
+           + OPS_LAUNCH * last["launched"]) / 32.0         # warp-instruction equivalents
+    props = torch.cuda.get_device_properties(local_rank)
+    max_mhz = clocks["sm_max_mhz"] or 2070.0
+    peak = props.multi_processor_count * ISSUE_PER_SM_CLK * max_mhz * 1e6
+    achieved = ops / (launch_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "spmc::transport_kernel<float,true>",
+                "peak_source": f"{props.multi_processor_count} SMs x {ISSUE_PER_SM_CLK} "
+                               f"warp-inst/clk x {max_mhz:.0f} MHz (max SM clock)",
+                "launch_ms": launch_ms,
+                "frac_at_measured_clock": (achieved / (peak * clocks["sm_mhz"] / max_mhz)
+                                           if clocks["sm_mhz"] else None)}
+
+    # end to end through the C ABI with host buffers: upload + pack the host
+    # mask, transport, normalise, copy the results back
+    host_mask = np.ascontiguousarray(mask)
+    e2e_times = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = spmc.Simulation(host_mask, MUS, MUA, G)
+        s2.run(args.photons, seed, stream)
+        s2.tallies(stream)
+        s2.close()
+        torch.cuda.synchronize()
+        if i:                                   # first pass is a warm-up
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times) if e2e_times else float("nan")
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "photons/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mask": "256x256x256", "porosity": POROSITY,
+                   "photons_per_step": args.photons, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "voxel_steps_per_s": value * steps_per_photon,
+        "steps_per_photon": steps_per_photon,
+        "interactions_per_photon": last["interactions"] / last["photons"],
+        "results": {k: last[k] for k in ("R", "T", "A", "closure", "phi_3d", "phi_1d",
+                                         "phi_pore", "r", "ratio", "identity_residual",
+                                         "pore_path_mean", "p_pore_gt_L")},
+        "roofline": roofline,
+        "e2e": {"value": args.photons * world / e2e_s, "unit": "photons/s",
+                "h2d_bytes_per_step": int(host_mask.nbytes),
+                "d2h_bytes_per_step": int(spmc.load().sp_mc_result_size())},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mask.copy(), target_s=args.cpu_seconds)
+        line["cpu_baseline"].pop("photons", None)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,777 @@
+// spmc_api.cu -- C ABI of libspmc: handle life cycle, mask bit-packing,
+// launches, and the FP64 normalisation of the integer tallies on the GPU.
+//
+// Normalisation (arXiv 2604.13929): R, T, A from independent counters
+// (Eq. RTA) with the closure of Eq. closure; fluence per unit incident flux
+// Phi/S0 = F nx ny / N (Eq. Phi_norm, steady source); <Phi>_3D over solid
+// voxels (Eq. Phi_MC3D), <Phi>_1D over all voxels (Eq. Phi_MC1D), the pore
+// mean, r (Eq. r_def), the concentration ratio and the residual of the
+// dilution identity (Eq. dilution); depth profiles per phase (App. B); the
+// exit-weighted pore-path statistics of Sec. 3.5(c).  Sums over voxels are
+// exact 128-bit integers; only the final divisions are floating point.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "spmc.h"
+#include "spmc_internal.cuh"
+
+using namespace spmc;
+
+// ------------------------------------------------------------ errors ----
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA,         \
+                        "%s: %s", #expr, cudaGetErrorString(e_));                       \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// ------------------------------------------------------------ handle ----
+
+struct sp_mc {
+    int device = 0, sm_count = 0;
+    int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0;
+    double voxel_h = 0, mus = 0, mua = 0, g = 0;   // mus, mua per voxel
+    u64 n_vox = 0, n_pore = 0;
+    double porosity = 0;
+    // options
+    double path_cap_opt = 0, rr_weight = 1e-4, rr_mult = 10.0;
+    int field = 1, precision = 32, blocks_opt = 0, threads = 256, smem_bricks_opt = 0;
+    u64 n_rec = 0, iter_limit_opt = 0, pid_offset = 0;
+    int compact_k = 8;
+    // device memory
+    u64 *d_bricks = nullptr, *d_field = nullptr, *d_layer = nullptr, *d_bin_count = nullptr;
+    DevTallies *d_tal = nullptr;
+    sp_mc_result_t *d_result = nullptr;
+    double *d_rec_sites = nullptr, *d_rec_vals = nullptr;
+    long long *d_rec_ints = nullptr;
+    u64 photons_done = 0;
+};
+
+static double default_path_cap(const sp_mc *h) {
+    // Eq. tend with n = 1 as a path length in voxels, EMA-scaled optics.
+    const double L = h->nz, solid = 1.0 - h->porosity;
+    const double s_abs = h->mua > 0 ? 5.0 / h->mua : 0.0;
+    const double s_diff = 18.0 * L * L * (h->mua + h->mus * (1.0 - h->g)) * solid;
+    return std::fmax(std::fmax(s_abs, s_diff), 4.0 * L);
+}
+
+static double path_cap(const sp_mc *h) {
+    return h->path_cap_opt > 0 ? h->path_cap_opt : default_path_cap(h);
+}
+
+static u64 iter_limit(const sp_mc *h) {
+    if (h->iter_limit_opt) return h->iter_limit_opt;
+    // face crossings per unit path <= sqrt(3) (plus ties), interactions ~ mu_s
+    const double s = path_cap(h);
+    const double lim = (3.0 * 1.7320508075688772 + 4.0 * h->mus + 1.0) * s + 1.0e4;
+    return lim > 4.0e9 ? 0xffffffffull : (u64)lim;
+}
+
+// --------------------------------------------------------- kernels ------
+
+// One thread per 4x4x4 brick: bit (lz*4+ly)*4+lx set for pore voxels;
+// bricks are z-major so the entry slab comes first.
+__global__ void pack_bricks_kernel(const uint8_t *__restrict__ mask, u64 *__restrict__ bricks,
+                                   int nx, int ny, int nz, int nbx, int nby, int nbz) {
+    const long long nb = (long long)nbx * nby * nbz;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+        u64 word = 0;
+        for (int lz = 0; lz < 4; ++lz) {
+            const int z = bz * 4 + lz;
+            if (z >= nz) break;
+            for (int ly = 0; ly < 4; ++ly) {
+                const int y = by * 4 + ly;
+                if (y >= ny) break;
+                const uint8_t *row = mask + ((size_t)z * ny + y) * (size_t)nx;
+                for (int lx = 0; lx < 4; ++lx) {
+                    const int x = bx * 4 + lx;
+                    if (x >= nx) break;
+                    if (row[x]) word |= 1ull << ((lz << 4) | (ly << 2) | lx);
+                }
+            }
+        }
+        bricks[b] = word;
+    }
+}
+
+__device__ __forceinline__ bool is_pore(const u64 *bricks, int nbx, int nby, int x, int y, int z) {
+    const u64 w = bricks[((size_t)(z >> 2) * nby + (y >> 2)) * nbx + (x >> 2)];
+    return (w >> (((z & 3) << 4) | ((y & 3) << 2) | (x & 3))) & 1ull;
+}
+
+__device__ __forceinline__ void add_u128(u64 &lo, u64 &hi, u64 vlo, u64 vhi) {
+    lo += vlo;
+    hi += vhi + (lo < vlo ? 1ull : 0ull);
+}
+
+// Exact per-layer sums of the Q32.32 field per phase: layer[z][phase][lo,hi].
+__global__ void layer_sums_kernel(const u64 *__restrict__ field, const u64 *__restrict__ bricks,
+                                  int nx, int ny, int nbx, int nby, u64 *__restrict__ layer,
+                                  DevTallies *tal) {
+    const int z = blockIdx.x;
+    const size_t nxy = (size_t)nx * ny;
+    const u64 *f = field + (size_t)z * nxy;
+    u64 lo[2] = {0, 0}, hi[2] = {0, 0};
+    bool big = false;
+    for (size_t i = threadIdx.x; i < nxy; i += blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i % nx);
+        const u64 val = f[i];
+        const int p = is_pore(bricks, nbx, nby, x, y, z) ? 1 : 0;
+        add_u128(lo[p], hi[p], val, 0);
+        big |= (val >> 62) != 0;
+    }
+    if (__syncthreads_or(big) && threadIdx.x == 0) atomicOr(&tal->flags, (u32)F_OVERFLOW);
+    __shared__ u64 s[32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int p = 0; p < 2; ++p) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const u64 ol = __shfl_down_sync(0xffffffffu, lo[p], o);
+            const u64 oh = __shfl_down_sync(0xffffffffu, hi[p], o);
+            add_u128(lo[p], hi[p], ol, oh);
+        }
+    }
+    if (lane == 0) { s[wid][0] = lo[0]; s[wid][1] = hi[0]; s[wid][2] = lo[1]; s[wid][3] = hi[1]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 a[4] = {0, 0, 0, 0};
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            add_u128(a[0], a[1], s[k][0], s[k][1]);
+            add_u128(a[2], a[3], s[k][2], s[k][3]);
+        }
+        for (int k = 0; k < 4; ++k) layer[(size_t)z * 4 + k] = a[k];
+    }
+}
+
+__device__ __forceinline__ double u128_to_double(u64 lo, u64 hi) {
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// FP64 normalisation and estimators; one block of 64 threads (one per bin).
+__global__ void finalize_kernel(const DevTallies *__restrict__ tal, const u64 *__restrict__ layer,
+                                const u64 *__restrict__ bin_count, int nx, int ny, int nz,
+                                double porosity, sp_mc_result_t *out) {
+    __shared__ u64 s_sum[2][kNBin][2];
+    const int b = threadIdx.x;
+    const double Q32 = 4294967296.0, Q16 = 65536.0;
+    double N = 0;
+    for (int k = 0; k < kNBatch; ++k) N += (double)tal->batch[k][B_PHOTONS];
+    const double scale = (double)nx * (double)ny / (N * Q32);
+
+    if (b < kNBin) {
+        u64 a[2][2] = {{0, 0}, {0, 0}};
+        if (layer) {
+            for (int z = 0; z < nz; ++z) {
+                if ((int)(((long long)z * kNBin) / nz) != b) continue;
+                add_u128(a[0][0], a[0][1], layer[(size_t)z * 4 + 0], layer[(size_t)z * 4 + 1]);
+                add_u128(a[1][0], a[1][1], layer[(size_t)z * 4 + 2], layer[(size_t)z * 4 + 3]);
+            }
+        } else {
+            for (int p = 0; p < 2; ++p) { a[p][0] = tal->depth[p][b][0]; a[p][1] = tal->depth[p][b][1]; }
+        }
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        u64 cnt_all = 0;
+        for (int p = 0; p < 2; ++p) {
+            s_sum[p][b][0] = a[p][0];
+            s_sum[p][b][1] = a[p][1];
+            out->raw_depth[p][b][0] = a[p][0];
+            out->raw_depth[p][b][1] = a[p][1];
+            const u64 c = bin_count[p * kNBin + b];
+            out->depth_count[p][b] = c;
+            cnt_all += c;
+            out->depth[p][b] = c ? u128_to_double(a[p][0], a[p][1]) * scale / (double)c : nan;
+        }
+        u64 lo = a[0][0], hi = a[0][1];
+        add_u128(lo, hi, a[1][0], a[1][1]);
+        out->depth[2][b] = cnt_all ? u128_to_double(lo, hi) * scale / (double)cnt_all : nan;
+    }
+    for (int i = b; i < kNHist; i += blockDim.x) {
+        out->raw_hist[i] = tal->hist[i];
+        out->pore_hist[i] = (double)tal->hist[i] / Q32 / N;
+    }
+    __syncthreads();
+    if (b != 0) return;
+
+    // weight budget and batch-means standard errors
+    const int slots[6] = {B_R, B_T, B_A, B_GATED, B_LOST, B_GAIN};
+    double tot[6];
+    double se[3];
+    for (int q = 0; q < 6; ++q) {
+        unsigned __int128 s = 0;
+        double m = 0, m2 = 0;
+        int nb = 0;
+        for (int k = 0; k < kNBatch; ++k) {
+            const u64 x = tal->batch[k][slots[q]];
+            s += x;
+            if (tal->batch[k][B_PHOTONS]) {
+                const double v = (double)x / Q32 / (double)tal->batch[k][B_PHOTONS];
+                m += v; m2 += v * v; ++nb;
+            }
+        }
+        tot[q] = u128_to_double((u64)s, (u64)(s >> 64)) / Q32 / N;
+        if (q < 3) {
+            const double mean = m / nb;
+            const double var = nb > 1 ? (m2 - nb * mean * mean) / (nb - 1) : 0.0 / 0.0;
+            se[q] = sqrt(fmax(var, 0.0) / nb);
+        }
+    }
+    out->R = tot[0]; out->T = tot[1]; out->A = tot[2];
+    out->gated = tot[3]; out->lost = tot[4]; out->gain = tot[5];
+    out->closure = tot[0] + tot[1] + tot[2] + tot[3] + tot[4] - tot[5];
+    out->R_se = se[0]; out->T_se = se[1]; out->A_se = se[2];
+    for (int k = 0; k < kNBatch; ++k) {
+        out->raw_R[k] = tal->batch[k][B_R];
+        out->raw_T[k] = tal->batch[k][B_T];
+        out->raw_A[k] = tal->batch[k][B_A];
+        out->raw_gated[k] = tal->batch[k][B_GATED];
+        out->raw_lost[k] = tal->batch[k][B_LOST];
+        out->raw_gain[k] = tal->batch[k][B_GAIN];
+        out->batch_photons[k] = tal->batch[k][B_PHOTONS];
+    }
+
+    // phase means (exact 128-bit totals, then FP64)
+    unsigned __int128 ts = 0, tp = 0;
+    u64 cs = 0, cp = 0;
+    for (int k = 0; k < kNBin; ++k) {
+        ts += ((unsigned __int128)s_sum[0][k][1] << 64) | s_sum[0][k][0];
+        tp += ((unsigned __int128)s_sum[1][k][1] << 64) | s_sum[1][k][0];
+        cs += bin_count[k];
+        cp += bin_count[kNBin + k];
+    }
+    const double sum_s = u128_to_double((u64)ts, (u64)(ts >> 64)) * scale;
+    const double sum_p = u128_to_double((u64)tp, (u64)(tp >> 64)) * scale;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    out->phi_3d = cs ? sum_s / (double)cs : nan;
+    out->phi_pore = cp ? sum_p / (double)cp : nan;
+    out->phi_1d = (sum_s + sum_p) / (double)(cs + cp);
+    out->r = out->phi_pore / out->phi_3d;
+    out->ratio = out->phi_3d / out->phi_1d;
+    out->identity_residual = out->ratio * (porosity * out->r + (1.0 - porosity)) - 1.0;
+
+    // exit-weighted pore path
+    const double sw = u128_to_double(tal->sums[0], tal->sums[1]);
+    const double swp = u128_to_double(tal->sums[2], tal->sums[3]);
+    const double swp2 = u128_to_double(tal->sums[4], tal->sums[5]);
+    out->escape_weight = sw / Q32 / N;
+    out->pore_path_mean = sw > 0 ? swp / sw : nan;
+    out->pore_path_m2 = sw > 0 ? (swp2 / Q16) / (sw / Q32) : nan;
+    double h_all = 0, h_gt = 0;
+    for (int k = 0; k < kNHist; ++k) {
+        h_all += (double)tal->hist[k];
+        if (k >= 64) h_gt += (double)tal->hist[k];
+    }
+    out->p_pore_gt_L = h_all > 0 ? h_gt / h_all : nan;
+    for (int k = 0; k < 2; ++k) {
+        out->raw_sum_w[k] = tal->sums[k];
+        out->raw_sum_wP[k] = tal->sums[2 + k];
+        out->raw_sum_wP2[k] = tal->sums[4 + k];
+    }
+    out->launched = tal->counts[C_LAUNCHED];
+    out->interactions = tal->counts[C_INTERACT];
+    out->scatters = tal->counts[C_SCATTER];
+    out->rr_survive = tal->counts[C_RR_SURV];
+    out->rr_kill = tal->counts[C_RR_KILL];
+    out->exit_R = tal->counts[C_EXIT_R];
+    out->exit_T = tal->counts[C_EXIT_T];
+    out->gated_n = tal->counts[C_GATED];
+    out->steps = tal->counts[C_STEPS];
+}
+
+template <typename T>
+__global__ void fluence_kernel(const u64 *__restrict__ field, T *__restrict__ out, size_t n,
+                               const DevTallies *__restrict__ tal, int nx, int ny) {
+    double N = 0;
+    for (int k = 0; k < kNBatch; ++k) N += (double)tal->batch[k][B_PHOTONS];
+    const double scale = (double)nx * (double)ny / (N * 4294967296.0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (T)((double)field[i] * scale);
+}
+
+// ------------------------------------------------------------ helpers ---
+
+static void free_all(sp_mc *h) {
+    cudaFree(h->d_bricks);
+    cudaFree(h->d_field);
+    cudaFree(h->d_layer);
+    cudaFree(h->d_bin_count);
+    cudaFree(h->d_tal);
+    cudaFree(h->d_result);
+    cudaFree(h->d_rec_sites);
+    cudaFree(h->d_rec_ints);
+    cudaFree(h->d_rec_vals);
+    h->d_bricks = h->d_field = h->d_layer = h->d_bin_count = nullptr;
+    h->d_tal = nullptr;
+    h->d_result = nullptr;
+    h->d_rec_sites = h->d_rec_vals = nullptr;
+    h->d_rec_ints = nullptr;
+}
+
+static int alloc_field(sp_mc *h) {
+    if (!h->field || h->d_field) return SP_OK;
+    CUDA_TRY(cudaMalloc(&h->d_field, h->n_vox * sizeof(u64)));
+    CUDA_TRY(cudaMemset(h->d_field, 0, h->n_vox * sizeof(u64)));
+    return SP_OK;
+}
+
+static int alloc_records(sp_mc *h, u64 n) {
+    cudaFree(h->d_rec_sites);
+    cudaFree(h->d_rec_ints);
+    cudaFree(h->d_rec_vals);
+    h->d_rec_sites = h->d_rec_vals = nullptr;
+    h->d_rec_ints = nullptr;
+    h->n_rec = 0;
+    if (!n) return SP_OK;
+    CUDA_TRY(cudaMalloc(&h->d_rec_sites, n * 24 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&h->d_rec_ints, n * 4 * sizeof(long long)));
+    CUDA_TRY(cudaMalloc(&h->d_rec_vals, n * 4 * sizeof(double)));
+    CUDA_TRY(cudaMemset(h->d_rec_sites, 0xff, n * 24 * sizeof(double)));   // NaN
+    CUDA_TRY(cudaMemset(h->d_rec_ints, 0, n * 4 * sizeof(long long)));
+    CUDA_TRY(cudaMemset(h->d_rec_vals, 0, n * 4 * sizeof(double)));
+    h->n_rec = n;
+    return SP_OK;
+}
+
+static int check_handle(const sp_mc *h) {
+    if (!h) return fail(SP_EINVAL, "null handle");
+    return SP_OK;
+}
+
+// --------------------------------------------------------------- ABI ----
+
+extern "C" {
+
+const char *sp_mc_last_error(void) { return g_err.c_str(); }
+
+const char *sp_mc_version(void) { return "spmc 0.1.0 sm_103a"; }
+
+size_t sp_mc_result_size(void) { return sizeof(sp_mc_result_t); }
+
+sp_mc_t *sp_mc_create(const uint8_t *mask, int nx, int ny, int nz, double voxel_h, double mu_s,
+                      double mu_a, double g) {
+    g_err.clear();
+    if (!mask) { fail(SP_EINVAL, "mask is NULL"); return nullptr; }
+    if (nx < 1 || ny < 1 || nz < 1) { fail(SP_EINVAL, "dimensions must be >= 1"); return nullptr; }
+    const u64 n_vox = (u64)nx * (u64)ny * (u64)nz;
+    if (n_vox >= (1ull << 40)) { fail(SP_EINVAL, "nx*ny*nz must be < 2^40"); return nullptr; }
+    if (!(voxel_h > 0) || !std::isfinite(voxel_h)) { fail(SP_EINVAL, "voxel_h must be > 0"); return nullptr; }
+    if (!(mu_s >= 0) || !(mu_a >= 0) || !std::isfinite(mu_s) || !std::isfinite(mu_a)) {
+        fail(SP_EINVAL, "mu_s and mu_a must be finite and >= 0");
+        return nullptr;
+    }
+    if (!(g > -1.0 && g < 1.0)) { fail(SP_EINVAL, "g must lie in (-1, 1)"); return nullptr; }
+
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1 || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        fail(SP_ECUDA, "no CUDA device available");
+        return nullptr;
+    }
+    sp_mc *h = new (std::nothrow) sp_mc();
+    if (!h) { fail(SP_ENOMEM, "host allocation failed"); return nullptr; }
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    h->nx = nx; h->ny = ny; h->nz = nz;
+    h->nbx = (nx + 3) / 4; h->nby = (ny + 3) / 4; h->nbz = (nz + 3) / 4;
+    h->voxel_h = voxel_h;
+    h->mus = mu_s * voxel_h;
+    h->mua = mu_a * voxel_h;
+    h->g = g;
+    h->n_vox = n_vox;
+
+    // voxel counts per (phase, depth bin), exact, on the host
+    std::vector<u64> cnt(2 * kNBin, 0);
+    u64 n_pore = 0;
+    for (int z = 0; z < nz; ++z) {
+        const uint8_t *layer = mask + (size_t)z * nx * ny;
+        u64 p = 0;
+        for (size_t i = 0; i < (size_t)nx * ny; ++i) p += layer[i] != 0;
+        const int b = (int)(((long long)z * kNBin) / nz);
+        cnt[kNBin + b] += p;
+        cnt[b] += (u64)nx * ny - p;
+        n_pore += p;
+    }
+    h->n_pore = n_pore;
+    h->porosity = (double)n_pore / (double)n_vox;
+
+    auto bail = [&](int code) -> sp_mc_t * {
+        (void)code;
+        free_all(h);
+        delete h;
+        return nullptr;
+    };
+    const u64 n_bricks = (u64)h->nbx * h->nby * h->nbz;
+    uint8_t *d_mask = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_mask, n_vox)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_bricks, n_bricks * sizeof(u64))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_tal, sizeof(DevTallies))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_result, sizeof(sp_mc_result_t))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_layer, (size_t)nz * 4 * sizeof(u64))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_bin_count, 2 * kNBin * sizeof(u64))) != cudaSuccess) {
+        cudaFree(d_mask);
+        fail(e == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA, "allocation: %s", cudaGetErrorString(e));
+        return bail(0);
+    }
+    // a1: upload and bit-pack the mask on the device
+    if ((e = cudaMemcpy(d_mask, mask, n_vox, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_bin_count, cnt.data(), cnt.size() * sizeof(u64), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(h->d_tal, 0, sizeof(DevTallies))) != cudaSuccess) {
+        cudaFree(d_mask);
+        fail(SP_ECUDA, "upload: %s", cudaGetErrorString(e));
+        return bail(0);
+    }
+    const int pack_blocks = (int)std::min<u64>((n_bricks + 255) / 256, 65535ull * 8);
+    pack_bricks_kernel<<<pack_blocks, 256>>>(d_mask, h->d_bricks, nx, ny, nz, h->nbx, h->nby, h->nbz);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        cudaFree(d_mask);
+        fail(SP_ECUDA, "mask packing: %s", cudaGetErrorString(e));
+        return bail(0);
+    }
+    cudaFree(d_mask);
+    if (alloc_field(h) != SP_OK) return bail(0);
+    return h;
+}
+
+void sp_mc_destroy(sp_mc_t *h) {
+    if (!h) return;
+    DeviceGuard guard(h->device);
+    free_all(h);
+    delete h;
+}
+
+int sp_mc_set_option(sp_mc_t *h, int key, double value) {
+    if (check_handle(h)) return SP_EINVAL;
+    DeviceGuard guard(h->device);
+    if (!std::isfinite(value)) return fail(SP_EINVAL, "option value must be finite");
+    switch (key) {
+    case SP_OPT_PATH_CAP: h->path_cap_opt = value; return SP_OK;
+    case SP_OPT_RR_WEIGHT:
+        if (value < 0) return fail(SP_EINVAL, "roulette threshold must be >= 0");
+        h->rr_weight = value; return SP_OK;
+    case SP_OPT_RR_MULT:
+        if (value < 1) return fail(SP_EINVAL, "roulette multiplier must be >= 1");
+        h->rr_mult = value; return SP_OK;
+    case SP_OPT_TALLY_FIELD: {
+        const int f = value != 0;
+        if (f == h->field) return SP_OK;
+        if (h->photons_done) return fail(SP_EINVAL, "tally mode can only change before the first run");
+        h->field = f;
+        if (!f) { cudaFree(h->d_field); h->d_field = nullptr; return SP_OK; }
+        return alloc_field(h);
+    }
+    case SP_OPT_PRECISION: {
+        const int p = (int)value;
+        if (p != 32 && p != 64) return fail(SP_EINVAL, "precision must be 32 or 64");
+        if (p != h->precision && h->photons_done)
+            return fail(SP_EINVAL, "precision can only change before the first run");
+        h->precision = p; return SP_OK;
+    }
+    case SP_OPT_RECORDS:
+        if (value < 0 || value > 1e8) return fail(SP_EINVAL, "records must be in [0, 1e8]");
+        if (h->photons_done) return fail(SP_EINVAL, "records can only be set before the first run");
+        return alloc_records(h, (u64)value);
+    case SP_OPT_BLOCKS:
+        if (value < 0 || value > 1e6) return fail(SP_EINVAL, "blocks out of range");
+        h->blocks_opt = (int)value; return SP_OK;
+    case SP_OPT_THREADS: {
+        const int t = (int)value;
+        if (t < 32 || t > 256 || t % 32) return fail(SP_EINVAL, "threads must be a multiple of 32 in [32, 256]");
+        h->threads = t; return SP_OK;
+    }
+    case SP_OPT_ITER_LIMIT:
+        if (value < 0) return fail(SP_EINVAL, "iteration limit must be >= 0");
+        h->iter_limit_opt = (u64)value; return SP_OK;
+    case SP_OPT_SMEM_BRICKS:
+        if (value < -1 || value > 1e7) return fail(SP_EINVAL, "smem bricks out of range");
+        h->smem_bricks_opt = (int)value; return SP_OK;
+    case SP_OPT_COMPACT:
+        if (value < 1 || value > 32) return fail(SP_EINVAL, "compaction threshold must be in [1, 32]");
+        h->compact_k = (int)value; return SP_OK;
+    case SP_OPT_PID_OFFSET:
+        if (value < 0 || value > 1.8e19) return fail(SP_EINVAL, "photon id offset out of range");
+        if (h->photons_done) return fail(SP_EINVAL, "the photon id offset can only be set before the first run");
+        h->pid_offset = (u64)value; return SP_OK;
+    default: return fail(SP_EINVAL, "unknown option %d", key);
+    }
+}
+
+int sp_mc_get_option(const sp_mc_t *h, int key, double *value) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (!value) return fail(SP_EINVAL, "value is NULL");
+    switch (key) {
+    case SP_OPT_PATH_CAP: *value = path_cap(h); return SP_OK;
+    case SP_OPT_RR_WEIGHT: *value = h->rr_weight; return SP_OK;
+    case SP_OPT_RR_MULT: *value = h->rr_mult; return SP_OK;
+    case SP_OPT_TALLY_FIELD: *value = h->field; return SP_OK;
+    case SP_OPT_PRECISION: *value = h->precision; return SP_OK;
+    case SP_OPT_RECORDS: *value = (double)h->n_rec; return SP_OK;
+    case SP_OPT_BLOCKS: *value = h->blocks_opt; return SP_OK;
+    case SP_OPT_THREADS: *value = h->threads; return SP_OK;
+    case SP_OPT_ITER_LIMIT: *value = (double)iter_limit(h); return SP_OK;
+    case SP_OPT_SMEM_BRICKS: *value = h->smem_bricks_opt; return SP_OK;
+    case SP_OPT_PID_OFFSET: *value = (double)h->pid_offset; return SP_OK;
+    case SP_OPT_COMPACT: *value = h->compact_k; return SP_OK;
+    default: return fail(SP_EINVAL, "unknown option %d", key);
+    }
+}
+
+int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (n_photons == 0) return SP_OK;
+    if (h->pid_offset + h->photons_done + n_photons < h->pid_offset + h->photons_done)
+        return fail(SP_EINVAL, "photon id overflow");
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(SP_ECUDA, "cannot select device %d", h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    const u64 n_bricks = (u64)h->nbx * h->nby * h->nbz;
+    int smem_bricks = h->smem_bricks_opt;
+    if (smem_bricks < 0) smem_bricks = (int)std::min<u64>(n_bricks, 12288);   // auto: 96 KiB
+    smem_bricks = (int)std::min<u64>((u64)smem_bricks, n_bricks);
+    const size_t smem = (size_t)smem_bricks * sizeof(u64);
+    const bool f64 = h->precision == 64;
+    const bool field = h->field != 0;
+    if (smem > 48 * 1024) {
+        CUDA_TRY(cudaFuncSetAttribute(f64 ? kernel_f64(field) : kernel_f32(field),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    int blocks = h->blocks_opt;
+    if (blocks <= 0) {
+        int per_sm = 0;
+        CUDA_TRY(f64 ? occupancy_f64(field, h->threads, smem, &per_sm)
+                     : occupancy_f32(field, h->threads, smem, &per_sm));
+        if (per_sm < 1) return fail(SP_ECUDA, "transport kernel cannot be resident with %zu B smem", smem);
+        blocks = per_sm * h->sm_count;
+    }
+
+    TransportParams p{};
+    p.bricks = h->d_bricks;
+    p.field = field ? h->d_field : nullptr;
+    p.tal = h->d_tal;
+    p.rec_sites = h->d_rec_sites;
+    p.rec_ints = h->d_rec_ints;
+    p.rec_vals = h->d_rec_vals;
+    p.n_rec = h->n_rec;
+    p.nx = h->nx; p.ny = h->ny; p.nz = h->nz;
+    p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz;
+    p.smem_bricks = smem_bricks;
+    p.key0 = (u32)seed;
+    p.key1 = (u32)(seed >> 32);
+    p.pid_begin = h->pid_offset + h->photons_done;
+    p.rec_base = h->pid_offset;
+    p.n_photons = n_photons;
+    p.mus = h->mus; p.mua = h->mua; p.g = h->g;
+    p.s_max = path_cap(h);
+    p.rr_weight = h->rr_weight;
+    p.rr_mult = h->rr_mult;
+    p.iter_limit = iter_limit(h);
+    p.compact_k = h->compact_k;
+    p.hg_iso = std::fabs(h->g) < 1e-6;
+    p.small_x = h->mua * 1.7320508075688772 <= 0.1;
+    p.f32.mus = (float)h->mus;
+    p.f32.mua = (float)h->mua;
+    p.f32.inv_mus = h->mus > 0 ? (float)(1.0 / h->mus) : 0.0f;
+    p.f32.inv_mua = h->mua > 0 ? (float)(1.0 / h->mua) : 0.0f;
+    {
+        const float gf = (float)h->g;       // the FP32 kernel's g, and expressions in FP32
+        p.f32.one_m_g2 = 1.0f - gf * gf;
+        p.f32.one_p_g2 = 1.0f + gf * gf;
+        p.f32.one_m_g = 1.0f - gf;
+        p.f32.two_g = 2.0f * gf;
+        p.f32.inv_2g = p.hg_iso ? 0.0f : (float)(1.0 / (2.0 * h->g));
+    }
+    p.f32.s_max = (float)p.s_max;
+    p.f32.rr_weight = (float)h->rr_weight;
+    p.f32.rr_mult = (float)h->rr_mult;
+    p.f32.rr_p = (float)(1.0 / h->rr_mult);
+    p.f32.rr_gain = (float)(h->rr_mult - 1.0);
+    p.f32.hist_scale = (float)(256.0 / (4.0 * (double)h->nz));
+
+    CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
+    CUDA_TRY(f64 ? launch_transport_f64(p, field, blocks, h->threads, smem, s)
+                 : launch_transport_f32(p, field, blocks, h->threads, smem, s));
+    h->photons_done += n_photons;
+    return SP_OK;
+}
+
+int sp_mc_tallies(sp_mc_t *h, sp_mc_result_t *out, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (!out) return fail(SP_EINVAL, "out is NULL");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->field) {
+        layer_sums_kernel<<<h->nz, 256, 0, s>>>(h->d_field, h->d_bricks, h->nx, h->ny, h->nbx, h->nby,
+                                                h->d_layer, h->d_tal);
+        CUDA_TRY(cudaGetLastError());
+    }
+    finalize_kernel<<<1, kNBin, 0, s>>>(h->d_tal, h->field ? h->d_layer : nullptr, h->d_bin_count,
+                                        h->nx, h->ny, h->nz, h->porosity, h->d_result);
+    CUDA_TRY(cudaGetLastError());
+    u32 flags = 0;
+    CUDA_TRY(cudaMemcpyAsync(out, h->d_result, sizeof(sp_mc_result_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&flags, &h->d_tal->flags, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    out->photons = h->photons_done;
+    out->precision = h->precision;
+    out->s_max = path_cap(h);
+    out->porosity = h->porosity;
+    out->status = SP_OK;
+    if (flags & F_ITER_LIMIT) out->status = SP_ESTEPLIMIT;
+    else if (flags & F_OVERFLOW) out->status = SP_EOVERFLOW;
+    if (out->status != SP_OK)
+        return fail(out->status, out->status == SP_ESTEPLIMIT ? "a photon hit the iteration limit"
+                                                              : "a voxel tally neared 2^62");
+    return SP_OK;
+}
+
+int sp_mc_fluence(sp_mc_t *h, void *dst, int dtype, int on_device, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (!dst) return fail(SP_EINVAL, "dst is NULL");
+    if (!h->field) return fail(SP_EINVAL, "the voxel field tally is disabled");
+    if (dtype != 0 && dtype != 1) return fail(SP_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
+    if (!h->photons_done) return fail(SP_EINVAL, "no photons have been run");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = h->n_vox * (dtype == 0 ? 8 : 4);
+    void *d_out = dst;
+    if (!on_device) CUDA_TRY(cudaMalloc(&d_out, bytes));
+    const int blocks = h->sm_count * 8;
+    if (dtype == 0) fluence_kernel<double><<<blocks, 256, 0, s>>>(h->d_field, (double *)d_out, h->n_vox, h->d_tal, h->nx, h->ny);
+    else fluence_kernel<float><<<blocks, 256, 0, s>>>(h->d_field, (float *)d_out, h->n_vox, h->d_tal, h->nx, h->ny);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMemcpyAsync(dst, d_out, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d_out);
+    }
+    if (e != cudaSuccess) return fail(SP_ECUDA, "fluence: %s", cudaGetErrorString(e));
+    return SP_OK;
+}
+
+int sp_mc_raw_field(sp_mc_t *h, uint64_t *dst, int on_device, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (!dst) return fail(SP_EINVAL, "dst is NULL");
+    if (!h->field) return fail(SP_EINVAL, "the voxel field tally is disabled");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(dst, h->d_field, h->n_vox * sizeof(u64),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(s));
+    return SP_OK;
+}
+
+int sp_mc_records(sp_mc_t *h, uint64_t n, double *sites, int64_t *ints, double *vals, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (n > h->n_rec) return fail(SP_EINVAL, "only %llu photons are recorded", (unsigned long long)h->n_rec);
+    if (!n) return SP_OK;
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (sites) CUDA_TRY(cudaMemcpyAsync(sites, h->d_rec_sites, n * 24 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (ints) CUDA_TRY(cudaMemcpyAsync(ints, h->d_rec_ints, n * 4 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    if (vals) CUDA_TRY(cudaMemcpyAsync(vals, h->d_rec_vals, n * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SP_OK;
+}
+
+int sp_mc_reset(sp_mc_t *h, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(h->d_tal, 0, sizeof(DevTallies), s));
+    if (h->d_field) CUDA_TRY(cudaMemsetAsync(h->d_field, 0, h->n_vox * sizeof(u64), s));
+    if (h->n_rec) {
+        CUDA_TRY(cudaMemsetAsync(h->d_rec_sites, 0xff, h->n_rec * 24 * sizeof(double), s));
+        CUDA_TRY(cudaMemsetAsync(h->d_rec_ints, 0, h->n_rec * 4 * sizeof(long long), s));
+        CUDA_TRY(cudaMemsetAsync(h->d_rec_vals, 0, h->n_rec * 4 * sizeof(double), s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    h->photons_done = 0;
+    return SP_OK;
+}
+
+// Checkpoint layout: header (magic, version, nx, ny, nz, field, photons_done),
+// the DevTallies block, then the Q32.32 field when enabled.
+struct CkptHeader {
+    u64 magic, version, nx, ny, nz, field, photons_done, tal_bytes;
+};
+static const u64 kMagic = 0x54504b43434d5053ull;   // "SPMCCKPT"
+
+size_t sp_mc_checkpoint_size(const sp_mc_t *h) {
+    if (!h) return 0;
+    return sizeof(CkptHeader) + sizeof(DevTallies) + (h->field ? h->n_vox * sizeof(u64) : 0);
+}
+
+int sp_mc_checkpoint(sp_mc_t *h, void *buf, size_t size, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (!buf || size < sp_mc_checkpoint_size(h)) return fail(SP_EINVAL, "checkpoint buffer too small");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CkptHeader hd{kMagic, 1, (u64)h->nx, (u64)h->ny, (u64)h->nz, (u64)h->field, h->photons_done,
+                  sizeof(DevTallies)};
+    std::memcpy(buf, &hd, sizeof hd);
+    char *p = static_cast<char *>(buf) + sizeof hd;
+    CUDA_TRY(cudaMemcpyAsync(p, h->d_tal, sizeof(DevTallies), cudaMemcpyDeviceToHost, s));
+    if (h->field)
+        CUDA_TRY(cudaMemcpyAsync(p + sizeof(DevTallies), h->d_field, h->n_vox * sizeof(u64),
+                                 cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SP_OK;
+}
+
+int sp_mc_restore(sp_mc_t *h, const void *buf, size_t size, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (!buf || size < sizeof(CkptHeader)) return fail(SP_EINVAL, "checkpoint too small");
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kMagic || hd.version != 1 || hd.tal_bytes != sizeof(DevTallies))
+        return fail(SP_EINVAL, "not a compatible checkpoint");
+    if (hd.nx != (u64)h->nx || hd.ny != (u64)h->ny || hd.nz != (u64)h->nz || hd.field != (u64)h->field)
+        return fail(SP_EINVAL, "checkpoint was taken on a different geometry or tally mode");
+    if (size < sp_mc_checkpoint_size(h)) return fail(SP_EINVAL, "checkpoint truncated");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const char *p = static_cast<const char *>(buf) + sizeof hd;
+    CUDA_TRY(cudaMemcpyAsync(h->d_tal, p, sizeof(DevTallies), cudaMemcpyHostToDevice, s));
+    if (h->field)
+        CUDA_TRY(cudaMemcpyAsync(h->d_field, p + sizeof(DevTallies), h->n_vox * sizeof(u64),
+                                 cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    h->photons_done = hd.photons_done;
+    return SP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// spmc_internal.cuh -- device-side data layout shared by the translation
+// units of libspmc (transport kernels, reductions, host API).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace spmc {
+
+using u64 = unsigned long long;
+using u32 = unsigned int;
+
+constexpr int kNBatch = 16;   // batch-means slots: photon id modulo 16
+constexpr int kNBin = 64;     // depth bins: floor(iz * 64 / nz)
+constexpr int kNHist = 257;   // pore-path histogram, 256 bins on [0, 4 nz) + overflow
+
+// Per-batch weight tallies (Q32.32) and photon counts.
+enum { B_R = 0, B_T, B_A, B_GATED, B_LOST, B_GAIN, B_PHOTONS, B_N = 8 };
+// Integer event counts.
+enum { C_LAUNCHED = 0, C_INTERACT, C_SCATTER, C_RR_SURV, C_RR_KILL, C_EXIT_R, C_EXIT_T,
+       C_GATED, C_STEPS, C_N = 16 };
+// Error flags raised by kernels.
+enum { F_ITER_LIMIT = 1u, F_OVERFLOW = 2u };
+
+// Global integer tallies of one simulation (zeroed at create / reset).
+// Every member is an exact integer sum, so the totals do not depend on the
+// order in which photons finish.
+struct DevTallies {
+    u64 batch[kNBatch][B_N];
+    u64 counts[C_N];
+    u64 hist[kNHist];
+    u64 sums[6];                   // 128-bit (lo, hi): sum q32(w), q32(w P), q16(w P^2)
+    u64 depth[2][kNBin][2];        // 128-bit (lo, hi) per phase and bin (profile mode)
+    u64 next;                      // photons claimed in the current launch
+    u32 flags;
+    u32 pad;
+};
+
+// Arguments of one transport launch.  Optics are per voxel (mu * h).
+struct TransportParams {
+    const u64 *bricks;             // 4x4x4 bit bricks, bit (lz*4+ly)*4+lx, 1 = pore
+    u64 *field;                    // Q32.32 track length per voxel, or nullptr
+    DevTallies *tal;
+    double *rec_sites;             // [n_rec][8][3]
+    long long *rec_ints;           // [n_rec][4]
+    double *rec_vals;              // [n_rec][4]
+    u64 n_rec;                     // records for photon ids [rec_base, rec_base + n_rec)
+    u64 rec_base;
+    int nx, ny, nz;
+    int nbx, nby, nbz;             // bricks per axis (ceil(n/4))
+    int smem_bricks;               // leading bricks (z-major) staged per CTA
+    u32 key0, key1;                // Philox key = seed
+    u64 pid_begin, n_photons;
+    double mus, mua, g;
+    double s_max, rr_weight, rr_mult;
+    u64 iter_limit;
+    int compact_k;                 // parked lanes per warp that trigger the event phase
+    int hg_iso;                    // |g| < 1e-6: isotropic scattering
+    int small_x;                   // mu_a * sqrt(3) <= 0.1: Taylor branch for 1 - exp(-x)
+    // The optics again as FP32, converted on the host: in FP32 kernels every
+    // constant is a float, so no double-to-float conversion (an FP64-pipe
+    // instruction) is ever rematerialised inside the loop.
+    struct F32 {
+        float mus, mua, inv_mus, inv_mua, one_m_g2, one_p_g2, one_m_g, two_g, inv_2g;
+        float s_max, rr_weight, rr_mult, rr_p, rr_gain, hist_scale;
+    } f32;
+};
+
+// Launch helpers (defined in the per-precision translation units).
+cudaError_t launch_transport_f32(const TransportParams &p, bool field, int blocks, int threads,
+                                 size_t smem, cudaStream_t s);
+cudaError_t launch_transport_f64(const TransportParams &p, bool field, int blocks, int threads,
+                                 size_t smem, cudaStream_t s);
+cudaError_t occupancy_f32(bool field, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_f64(bool field, int threads, size_t smem, int *blocks_per_sm);
+const void *kernel_f32(bool field);
+const void *kernel_f64(bool field);
+
+}  // namespace spmc

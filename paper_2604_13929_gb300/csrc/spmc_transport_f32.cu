@@ -1,0 +1,17 @@
+// spmc_transport_f32.cu -- float instantiation of the transport kernel.
+#include "spmc_transport.cuh"
+
+namespace spmc {
+
+cudaError_t launch_transport_f32(const TransportParams &p, bool field, int blocks, int threads,
+                                 size_t smem, cudaStream_t s) {
+    return launch_transport<float>(p, field, blocks, threads, smem, s);
+}
+
+cudaError_t occupancy_f32(bool field, int threads, size_t smem, int *blocks_per_sm) {
+    return occupancy<float>(field, threads, smem, blocks_per_sm);
+}
+
+const void *kernel_f32(bool field) { return kernel_ptr<float>(field); }
+
+}  // namespace spmc

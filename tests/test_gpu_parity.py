@@ -1,0 +1,415 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Same photon streams: Philox4x32-10 keyed by (seed, photon id) on both sides,
+so the GPU and the oracle run the same photons; the FP32 transport may only
+differ by rounding.  Tolerances: R/T/A and >= 99 % of the depth-bin fluences
+within 4 combined standard errors and 0.2 % absolute; integer event counts
+exactly equal for the FP64 transport, >= 99.9 % per-photon agreement for FP32;
+the first 8 interaction sites within 1e-5 * max(|position|, 1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2604_13929_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+Q32 = 2.0 ** 32
+C1_SEED = 20260809          # the paper's MC seed (App. B)
+MUS, MUA, G = 0.5, 0.005, 0.7
+
+
+@pytest.fixture(scope="module")
+def spmc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_13929_gb300 import build
+    build.build()
+    from paper_2604_13929_gb300 import spmc as s
+    return s
+
+
+@pytest.fixture(scope="module")
+def c1_mask():
+    """64^3 Cahn-Hilliard mask, 1000 steps, porosity 0.70, mask seed 0."""
+    return inputs.spinodal_mask(64, 0.70, 1000, seed=0, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def c2_mask():
+    """256^3 Cahn-Hilliard mask, 4000 steps, porosity 0.90, mask seed 0."""
+    return inputs.spinodal_mask(256, 0.90, 4000, seed=0, device="cuda")
+
+
+def _u128(raw):
+    raw = np.asarray(raw, dtype=np.uint64)
+    return raw[..., 0].astype(np.float64) + raw[..., 1].astype(np.float64) * 2.0 ** 64
+
+
+def _gpu_chunked(sim, mask, n, seed, k=16):
+    """Run n photons as k consecutive chunks; per-chunk depth profiles for
+    batch-means standard errors (chunks are contiguous photon-id blocks)."""
+    nz, ny, nx = mask.shape
+    cnt = orc.phase_counts(mask)
+    prev = np.zeros((2, 64))
+    per = []
+    for _ in range(k):
+        sim.run(n // k, seed)
+        t = sim.tallies()
+        cur = _u128(t["raw_depth"])
+        with np.errstate(invalid="ignore", divide="ignore"):
+            per.append((cur - prev) * nx * ny / ((n // k) * Q32) / cnt)
+        prev = cur
+    per = np.array(per)
+    return t, per.std(axis=0, ddof=1) / math.sqrt(k)
+
+
+def _assert_rta(g, o, label=""):
+    for k in ("R", "T", "A"):
+        se = math.hypot(g[k + "_se"], o[k + "_se"])
+        assert abs(g[k] - o[k]) <= 4 * se + 0.002, (label, k, g[k], o[k], se)
+
+
+def _assert_depth(gd, gse, od, ose, frac=0.99):
+    ok = np.isfinite(od) & np.isfinite(gd)
+    diff = np.abs(gd - od)[ok]
+    tol = (4 * np.hypot(gse, ose) + 0.002 * np.abs(od))[ok]
+    assert (diff <= tol).mean() >= frac, (diff / np.maximum(tol, 1e-300)).max()
+
+
+# ------------------------------------------------------------------ parity --
+
+def test_c1_same_streams_fp32(spmc, c1_mask):
+    """64^3 spinodal, phi = 0.70, 2e5 photons: GPU FP32 vs oracle FP64."""
+    n = 200000
+    sim = spmc.Simulation(c1_mask, MUS, MUA, G)
+    g, gse = _gpu_chunked(sim, c1_mask, n, C1_SEED)
+    res = orc.run(c1_mask, MUS, MUA, G, n, C1_SEED)
+    o = orc.normalise(res)
+    _assert_rta(g, o)
+    _assert_depth(g["depth"][:2], gse, o["depth"], o["depth_se"])
+    # same photons: far tighter than the statistical bar
+    for k in ("R", "T", "A"):
+        assert abs(g[k] - o[k]) < 2e-4, k
+    assert g["launched"] == n
+    for k in ("interactions", "exit_R", "exit_T", "rr_kill", "gated"):
+        ok = o["counts"][k] if k != "gated" else o["counts"]["gated"]
+        gk = g[k] if k != "gated" else g["gated_n"]
+        assert abs(gk - ok) <= max(3, 1e-3 * ok), (k, gk, ok)
+    assert abs(g["closure"] - 1) < 1e-6
+    assert abs(g["identity_residual"]) < 1e-12
+    for k in ("phi_3d", "phi_1d", "phi_pore", "r", "ratio", "porosity"):
+        assert abs(g[k] / o[k] - 1) < 2e-3, k
+    assert abs(g["pore_path_mean"] / o["pore_path_mean"] - 1) < 2e-3
+    # absorbed weight equals mu_a times the solid track length
+    field = sim.raw_field()
+    solid_track = orc.exact_sum(field[c1_mask == 0]) / Q32
+    assert abs(orc.exact_sum(g["raw_A"]) / Q32 - MUA * solid_track) < 1e-5 * n
+    sim.close()
+
+
+def test_c1_independent_streams_statistics(spmc, c1_mask):
+    """Different seeds: agreement within 4 combined SE and 0.2 % absolute."""
+    sim = spmc.Simulation(c1_mask, MUS, MUA, G)
+    g, gse = _gpu_chunked(sim, c1_mask, 1600000, 99)
+    o = orc.normalise(orc.run(c1_mask, MUS, MUA, G, 200000, C1_SEED))
+    _assert_rta(g, o)
+    _assert_depth(g["depth"][:2], gse, o["depth"], o["depth_se"])
+    sim.close()
+
+
+def _first_sites_agree(gs, gi, os_, oi):
+    """Per photon: the first min(8, events) interaction sites agree within
+    1e-5 * max(|position|, 1), and both sides record the same number of them."""
+    n = gi.shape[0]
+    kg, ko = np.minimum(gi[:, 0], 8), np.minimum(oi[:, 0], 8)
+    tol = 1e-5 * np.maximum(np.linalg.norm(os_, axis=2), 1.0)
+    err = np.linalg.norm(gs - os_, axis=2)
+    ok = np.array([kg[i] == ko[i] and np.all(err[i, :ko[i]] <= tol[i, :ko[i]])
+                   for i in range(n)])
+    return ok
+
+
+def test_first_eight_interaction_sites(spmc, c1_mask):
+    """The first 8 interaction sites of each photon, GPU vs oracle, within
+    1e-5 * max(|position|, 1).  FP64 transport: >= 99.9 % of photons (in
+    practice all).  FP32 transport: >= 99 %; the rest diverge because every
+    crossing of a solid/pore interface changes the optical depth consumed by
+    an amount proportional to the position error, so rounding differences
+    grow along a history until a discrete event (which voxel an interaction
+    falls in) flips.  Whole-history agreement is bounded the same way."""
+    n = 10000
+    o = orc.run(c1_mask, MUS, MUA, G, n, C1_SEED, n_rec=n)
+    rates = {}
+    for prec in (32, 64):
+        sim = spmc.Simulation(c1_mask, MUS, MUA, G, records=n, precision=prec)
+        sim.run(n, C1_SEED)
+        gs, gi, gv = sim.records(n)
+        sim.close()
+        ok = _first_sites_agree(gs, gi, o["rec_sites"], o["rec_ints"])
+        same = (gi[:, 0] == o["rec_ints"][:, 0]) & (gi[:, 2] == o["rec_ints"][:, 2])
+        rates[prec] = (ok.mean(), same.mean())
+        # unused slots stay NaN
+        assert np.all(np.isnan(gs[np.arange(8)[None, :] >= np.minimum(gi[:, :1], 8)]))
+    assert rates[64][0] >= 0.999 and rates[64][1] >= 0.999, rates
+    assert rates[32][0] >= 0.99 and rates[32][1] >= 0.97, rates
+
+
+def test_fp64_transport_matches_oracle_per_photon(spmc):
+    """FP64 transport on a random (tie-free) mask: the first 8 sites agree to
+    1e-9 and whole histories (event counts, exit kind, roulette survivals)
+    agree for >= 99.9 % of photons; aggregate integer counts within 0.1 %."""
+    mask = inputs.random_mask((22, 13, 10), 0.55, 9)
+    n = 20000
+    sim = spmc.Simulation(mask, 0.7, 0.02, 0.6, precision=64, records=n)
+    sim.run(n, 4242)
+    g = sim.tallies()
+    gs, gi, gv = sim.records(n)
+    o = orc.run(mask, 0.7, 0.02, 0.6, n, 4242, n_rec=n)
+    same = np.all(gi == o["rec_ints"], axis=1)
+    assert same.mean() >= 0.999, np.nonzero(~same)[0][:10]
+    fin = np.isfinite(o["rec_sites"]) & np.isfinite(gs)
+    close = np.all(np.abs(np.where(fin, gs - o["rec_sites"], 0)) <= 1e-9, axis=(1, 2))
+    assert (close | ~same).all() or close.mean() >= 0.999
+    vclose = np.all(np.isclose(gv, o["rec_vals"], rtol=1e-6, atol=1e-12), axis=1)
+    assert vclose.mean() >= 0.999
+    for k in ("launched", "interactions", "scatters", "rr_kill", "exit_R", "exit_T", "steps"):
+        assert abs(g[k] - o["counts"][k]) <= max(2, 1e-3 * o["counts"][k]), (k, g[k], o["counts"][k])
+    sim.close()
+
+
+@pytest.mark.parametrize("pattern", [None, [1, 0, 0, 1, 1, 0, 1, 0, 0, 0, 1, 0, 1, 1]])
+def test_fp64_transport_exact_on_interface_free_geometry(spmc, pattern):
+    """Homogeneous and laterally uniform layered slabs have no lateral
+    interfaces to amplify last-ulp differences: there the FP64 transport
+    reproduces the oracle's integer event counts exactly, photon by photon."""
+    mask = inputs.all_solid(12, 3, 5) if pattern is None else inputs.layered(pattern, 4, 3)
+    n = 20000
+    sim = spmc.Simulation(mask, 0.6, 0.03, 0.7, precision=64, records=n)
+    sim.run(n, 99)
+    g = sim.tallies()
+    _, gi, _ = sim.records(n)
+    o = orc.run(mask, 0.6, 0.03, 0.7, n, 99, n_rec=n)
+    assert np.array_equal(gi, o["rec_ints"])
+    for k in ("launched", "interactions", "scatters", "rr_survive", "rr_kill", "exit_R",
+              "exit_T", "steps"):
+        assert g[k] == o["counts"][k], k
+    assert g["gated_n"] == o["counts"]["gated"]
+    for k in ("R", "T", "A", "gated", "lost", "gain"):
+        assert np.all(np.abs(g["raw_" + k].astype(np.int64) - o[k].astype(np.int64)) <= 2 * n // 16 + 1)
+    sim.close()
+
+
+# ------------------------------------------------------------ closed forms --
+
+@pytest.mark.parametrize("precision,tol", [(32, 2e-6), (64, 1e-10)])
+def test_pure_absorption_closed_form(spmc, precision, tol):
+    nz, mua = 20, 0.05
+    sim = spmc.Simulation(inputs.all_solid(nz, 6, 5), 0.0, mua, 0.7, precision=precision)
+    sim.run(50000, 3)
+    t = sim.tallies()
+    assert abs(t["T"] - math.exp(-mua * nz)) < tol
+    assert t["R"] == 0 and t["interactions"] == 0
+    assert abs(t["A"] - (1 - math.exp(-mua * nz))) < tol
+    layer = sim.raw_field().reshape(nz, -1).sum(axis=1).astype(np.float64) / Q32 / 50000
+    expect = np.exp(-mua * np.arange(nz)) * (1 - math.exp(-mua)) / mua
+    assert np.allclose(layer, expect, rtol=10 * tol)
+    sim.close()
+
+
+def test_all_pore_unit_fluence_exact(spmc):
+    nz, n = 37, 30000
+    sim = spmc.Simulation(inputs.all_pore(nz, 9, 11), MUS, MUA, G)
+    sim.run(n, 5)
+    t = sim.tallies()
+    assert t["T"] == 1.0 and t["R"] == 0.0 and t["A"] == 0.0
+    f = sim.raw_field()
+    assert all(orc.exact_sum(f[z]) == n * 2 ** 32 for z in range(nz))
+    assert np.all(t["depth"][1][np.unique((np.arange(nz) * 64) // nz)] == 1.0)
+    assert t["pore_path_mean"] == nz and t["raw_hist"][64] == n * 2 ** 32
+    sim.close()
+
+
+def test_path_cap_gates_exactly(spmc):
+    nz, n = 64, 10000
+    sim = spmc.Simulation(inputs.all_pore(nz, 4, 4), MUS, MUA, G, path_cap=32.5)
+    sim.run(n, 5)
+    t = sim.tallies()
+    assert t["gated"] == 1.0 and t["T"] == 0.0 and t["closure"] == 1.0
+    f = sim.raw_field()
+    layer = [orc.exact_sum(f[z]) for z in range(nz)]
+    assert all(v == n * 2 ** 32 for v in layer[:32]) and layer[32] == n * 2 ** 31
+    assert all(v == 0 for v in layer[33:])
+    sim.close()
+
+
+def test_slab_matches_oracle_and_transport_solver(spmc):
+    from rte_slab import SlabSolution
+    nz = 12
+    with np.errstate(over="ignore"):
+        sol = SlabSolution(0.5, 0.05, 0.7, nz)
+    sim = spmc.Simulation(inputs.all_solid(nz, 4, 4), 0.5, 0.05, 0.7)
+    sim.run(4000000, 77)
+    t = sim.tallies()
+    for k, ref in (("R", sol.reflectance()), ("T", sol.transmittance()),
+                   ("A", sol.absorptance())):
+        assert abs(t[k] - ref) < 4 * t[k + "_se"] + 1e-4, k
+    sim.close()
+
+
+# ------------------------------------------------------------- determinism --
+
+def test_bitwise_determinism_across_runs_configs_and_splits(spmc, c1_mask):
+    n = 100000
+
+    def run(**opt):
+        sim = spmc.Simulation(c1_mask, MUS, MUA, G, **{k: v for k, v in opt.items()
+                                                         if k != "split"})
+        if opt.get("split"):
+            sim.run(37000, 11).run(n - 37000, 11)
+        else:
+            sim.run(n, 11)
+        t = sim.tallies()
+        f = sim.raw_field()
+        sim.close()
+        return t, f
+
+    base_t, base_f = run()
+    for opt in ({}, {"threads": 128}, {"blocks": 37, "threads": 64}, {"split": True},
+                {"smem_bricks": 2048}, {"compact": 1}, {"compact": 32}):
+        t, f = run(**opt)
+        assert np.array_equal(f, base_f), opt
+        for k in ("raw_R", "raw_T", "raw_A", "raw_gated", "raw_lost", "raw_gain", "raw_hist",
+                  "raw_depth", "raw_sum_wP"):
+            assert np.array_equal(t[k], base_t[k]), (opt, k)
+        assert t["steps"] == base_t["steps"] and t["interactions"] == base_t["interactions"]
+
+
+def test_profile_mode_depth_tallies_equal_field_sums(spmc, c1_mask):
+    a = spmc.Simulation(c1_mask, MUS, MUA, G)
+    b = spmc.Simulation(c1_mask, MUS, MUA, G, tally_field=0)
+    a.run(50000, 8)
+    b.run(50000, 8)
+    ta, tb = a.tallies(), b.tallies()
+    assert np.array_equal(ta["raw_depth"], tb["raw_depth"])
+    assert np.array_equal(ta["raw_R"], tb["raw_R"])
+    a.close()
+    b.close()
+
+
+def test_checkpoint_restore_continues_bitwise(spmc, c1_mask):
+    a = spmc.Simulation(c1_mask, MUS, MUA, G)
+    a.run(30000, 3)
+    ck = a.checkpoint()
+    a.run(20000, 3)
+    b = spmc.Simulation(c1_mask, MUS, MUA, G)
+    b.restore(ck)
+    b.run(20000, 3)
+    ta, tb = a.tallies(), b.tallies()
+    assert np.array_equal(a.raw_field(), b.raw_field())
+    assert np.array_equal(ta["raw_R"], tb["raw_R"]) and ta["photons"] == tb["photons"] == 50000
+    a.close()
+    b.close()
+
+
+# ----------------------------------------------------------- edge cases --
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 1, 1), (1, 7, 3), (9, 6, 5), (13, 2, 30)])
+def test_ragged_and_degenerate_shapes(spmc, shape):
+    mask = inputs.random_mask(shape, 0.5, 1)
+    n = 20000
+    sim = spmc.Simulation(mask, 0.6, 0.03, 0.5, precision=64)
+    sim.run(n, 2)
+    g = sim.tallies()
+    o = orc.run(mask, 0.6, 0.03, 0.5, n, 2)
+    for k in ("launched", "interactions", "exit_R", "exit_T", "rr_kill"):
+        assert g[k] == o["counts"][k], (shape, k)
+    assert abs(g["closure"] - 1) < 1e-9
+    sim.close()
+
+
+def test_zero_photons_and_errors(spmc, c1_mask):
+    sim = spmc.Simulation(c1_mask, MUS, MUA, G)
+    sim.run(0, 1)
+    assert sim.tallies()["photons"] == 0
+    with pytest.raises(spmc.SpmcError):
+        sim.set_option("precision", 16)
+    with pytest.raises(spmc.SpmcError):
+        sim.set_option("threads", 1000)
+    sim.run(10, 1)
+    with pytest.raises(spmc.SpmcError):
+        sim.set_option("tally_field", 0)      # only before the first run
+    sim.close()
+
+
+def test_iteration_limit_reports_status_and_keeps_budget(spmc, c1_mask):
+    sim = spmc.Simulation(c1_mask, MUS, MUA, G, iter_limit=5)
+    sim.run(5000, 1)
+    t = sim.tallies(check=False)
+    assert t["status"] == spmc.SP_ESTEPLIMIT
+    assert abs(t["closure"] - 1) < 1e-6 and t["gated"] > 0.5
+    with pytest.raises(spmc.SpmcError) as e:
+        sim.tallies()
+    assert e.value.code == spmc.SP_ESTEPLIMIT
+    sim.close()
+
+
+def test_fluence_outputs_host_and_device(spmc, c1_mask):
+    import torch
+    sim = spmc.Simulation(c1_mask, MUS, MUA, G)
+    sim.run(20000, 6)
+    raw = sim.raw_field().astype(np.float64) * 64 * 64 / (20000 * Q32)
+    h64 = sim.fluence()
+    d32 = torch.empty(c1_mask.shape, dtype=torch.float32, device="cuda")
+    sim.fluence(d32)
+    assert np.allclose(h64, raw, rtol=1e-15, atol=0)
+    assert np.allclose(d32.cpu().numpy(), raw, rtol=1e-6)
+    t = sim.tallies()
+    assert abs(h64[c1_mask == 0].mean() / t["phi_3d"] - 1) < 1e-12
+    assert abs(h64.mean() / t["phi_1d"] - 1) < 1e-12
+    sim.close()
+
+
+# ------------------------------------------------------------ full size --
+
+def test_c2_full_size_properties_and_sampled_photons(spmc, c2_mask):
+    """256^3, phi = 0.90, 1e8 photons in the benchmark's launch
+    configuration: budget closure, dilution identity, per-photon agreement
+    of a sampled block of photons with the oracle, and R/T/A against an
+    oracle sample within 4 combined SE + 0.2 %."""
+    n, n_rec = 100_000_000, 2000
+    sim = spmc.Simulation(c2_mask, MUS, MUA, G, records=n_rec)
+    sim.run(n, C1_SEED)
+    g = sim.tallies()
+    assert g["photons"] == n and g["launched"] == n and g["status"] == 0
+    assert abs(g["closure"] - 1) < 1e-6
+    assert abs(g["identity_residual"]) < 1e-12
+    gs, gi, _ = sim.records(n_rec)
+    o = orc.run(c2_mask, MUS, MUA, G, n_rec, C1_SEED, n_rec=n_rec)
+    ok = _first_sites_agree(gs, gi, o["rec_sites"], o["rec_ints"])
+    assert ok.mean() >= 0.99, (~ok).sum()
+    s64 = spmc.Simulation(c2_mask, MUS, MUA, G, records=n_rec, precision=64)
+    s64.run(n_rec, C1_SEED)
+    gs64, gi64, _ = s64.records(n_rec)
+    s64.close()
+    ok64 = _first_sites_agree(gs64, gi64, o["rec_sites"], o["rec_ints"])
+    assert ok64.mean() >= 0.999, (~ok64).sum()
+    os_ = orc.normalise(orc.run(c2_mask, MUS, MUA, G, 100000, 1, field=False))
+    _assert_rta(g, os_, "c2")
+    sim.close()
+
+
+def test_max_size_512_cubed_runs(spmc):
+    """512^3 bit-packed mask (16 MiB) and 1 GiB Q32.32 field: 64-bit voxel
+    indexing over the whole volume."""
+    mask = inputs.random_mask((512, 512, 512), 0.9, 5)
+    sim = spmc.Simulation(mask, MUS, MUA, G)
+    sim.run(2_000_000, 1)
+    t = sim.tallies()
+    assert abs(t["closure"] - 1) < 1e-6 and abs(t["identity_residual"]) < 1e-12
+    assert t["T"] > 0 and t["depth_count"].sum() == 512 ** 3
+    sim.close()
