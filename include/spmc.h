@@ -119,13 +119,14 @@ typedef struct {
  * Create a simulation over a binary mask.
  *   mask      host pointer, nz*ny*nx bytes, x fastest ([iz][iy][ix]);
  *             nonzero = pore (void), 0 = solid.  Copied; the caller keeps it.
- *   nx,ny,nz  >= 1 each, nx*ny*nz < 2^40.
+ *   nx,ny,nz  >= 1 each, fewer than 2^31 4x4x4 bricks (about 2^37 voxels).
  *   voxel_h   voxel edge (> 0) in the length unit of mu_s, mu_a.
  *   mu_s,mu_a solid scattering / absorption coefficients (>= 0, finite).
  *   g         HG anisotropy, -1 < g < 1.
  * Uses the current CUDA device.  Returns NULL on failure (see
  * sp_mc_last_error()).  Device memory: the bit-packed mask (1 bit/voxel),
- * the voxel fluence field (8 bytes/voxel, when enabled) and a few KiB.
+ * the voxel fluence field (8 bytes/voxel over the volume padded to
+ * multiples of 4, when enabled) and a few KiB.
  */
 sp_mc_t *sp_mc_create(const uint8_t *mask, int nx, int ny, int nz, double voxel_h,
                       double mu_s, double mu_a, double g);

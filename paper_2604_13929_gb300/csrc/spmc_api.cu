@@ -16,6 +16,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "spmc.h"
@@ -64,6 +65,7 @@ struct sp_mc {
     int nx = 0, ny = 0, nz = 0, nbx = 0, nby = 0, nbz = 0;
     double voxel_h = 0, mus = 0, mua = 0, g = 0;   // mus, mua per voxel
     u64 n_vox = 0, n_pore = 0;
+    u64 n_field = 0;        // padded voxels of the brick-layout field: 64 per brick
     double porosity = 0;
     // options
     double path_cap_opt = 0, rr_weight = 1e-4, rr_mult = 10.0;
@@ -133,6 +135,13 @@ __device__ __forceinline__ bool is_pore(const u64 *bricks, int nbx, int nby, int
     return (w >> (((z & 3) << 4) | ((y & 3) << 2) | (x & 3))) & 1ull;
 }
 
+// Offset of voxel (x, y, z) in the brick-layout field: 64 consecutive words
+// per 4x4x4 brick, bricks z-major, the same bit order as the mask bricks.
+__device__ __forceinline__ u64 field_index(int nbx, int nby, int x, int y, int z) {
+    const u64 b = ((u64)(z >> 2) * (u64)nby + (u64)(y >> 2)) * (u64)nbx + (u64)(x >> 2);
+    return (b << 6) | (u64)(((z & 3) << 4) | ((y & 3) << 2) | (x & 3));
+}
+
 __device__ __forceinline__ void add_u128(u64 &lo, u64 &hi, u64 vlo, u64 vhi) {
     lo += vlo;
     hi += vhi + (lo < vlo ? 1ull : 0ull);
@@ -144,12 +153,11 @@ __global__ void layer_sums_kernel(const u64 *__restrict__ field, const u64 *__re
                                   DevTallies *tal) {
     const int z = blockIdx.x;
     const size_t nxy = (size_t)nx * ny;
-    const u64 *f = field + (size_t)z * nxy;
     u64 lo[2] = {0, 0}, hi[2] = {0, 0};
     bool big = false;
     for (size_t i = threadIdx.x; i < nxy; i += blockDim.x) {
         const int y = (int)(i / nx), x = (int)(i % nx);
-        const u64 val = f[i];
+        const u64 val = field[field_index(nbx, nby, x, y, z)];
         const int p = is_pore(bricks, nbx, nby, x, y, z) ? 1 : 0;
         add_u128(lo[p], hi[p], val, 0);
         big |= (val >> 62) != 0;
@@ -310,15 +318,25 @@ __global__ void finalize_kernel(const DevTallies *__restrict__ tal, const u64 *_
     out->steps = tal->counts[C_STEPS];
 }
 
+// Field in x-fastest order: Phi/S0 as float/double, or the raw Q32.32 words
+// (T = u64, no scaling).
 template <typename T>
-__global__ void fluence_kernel(const u64 *__restrict__ field, T *__restrict__ out, size_t n,
-                               const DevTallies *__restrict__ tal, int nx, int ny) {
-    double N = 0;
-    for (int k = 0; k < kNBatch; ++k) N += (double)tal->batch[k][B_PHOTONS];
-    const double scale = (double)nx * (double)ny / (N * 4294967296.0);
+__global__ void fluence_kernel(const u64 *__restrict__ field, T *__restrict__ out, int nx, int ny,
+                               int nz, int nbx, int nby, const DevTallies *__restrict__ tal) {
+    double scale = 1.0;
+    if constexpr (!std::is_same<T, u64>::value) {
+        double N = 0;
+        for (int k = 0; k < kNBatch; ++k) N += (double)tal->batch[k][B_PHOTONS];
+        scale = (double)nx * (double)ny / (N * 4294967296.0);
+    }
+    const size_t n = (size_t)nx * ny * nz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (T)((double)field[i] * scale);
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const u64 val = field[field_index(nbx, nby, x, y, z)];
+        if constexpr (std::is_same<T, u64>::value) out[i] = val;
+        else out[i] = (T)((double)val * scale);
+    }
 }
 
 // ------------------------------------------------------------ helpers ---
@@ -342,8 +360,8 @@ static void free_all(sp_mc *h) {
 
 static int alloc_field(sp_mc *h) {
     if (!h->field || h->d_field) return SP_OK;
-    CUDA_TRY(cudaMalloc(&h->d_field, h->n_vox * sizeof(u64)));
-    CUDA_TRY(cudaMemset(h->d_field, 0, h->n_vox * sizeof(u64)));
+    CUDA_TRY(cudaMalloc(&h->d_field, h->n_field * sizeof(u64)));
+    CUDA_TRY(cudaMemset(h->d_field, 0, h->n_field * sizeof(u64)));
     return SP_OK;
 }
 
@@ -386,7 +404,8 @@ sp_mc_t *sp_mc_create(const uint8_t *mask, int nx, int ny, int nz, double voxel_
     if (!mask) { fail(SP_EINVAL, "mask is NULL"); return nullptr; }
     if (nx < 1 || ny < 1 || nz < 1) { fail(SP_EINVAL, "dimensions must be >= 1"); return nullptr; }
     const u64 n_vox = (u64)nx * (u64)ny * (u64)nz;
-    if (n_vox >= (1ull << 40)) { fail(SP_EINVAL, "nx*ny*nz must be < 2^40"); return nullptr; }
+    const u64 n_bricks_req = (u64)((nx + 3) / 4) * (u64)((ny + 3) / 4) * (u64)((nz + 3) / 4);
+    if (n_bricks_req >= (1ull << 31)) { fail(SP_EINVAL, "the volume must have fewer than 2^31 4x4x4 bricks (about 2^37 voxels)"); return nullptr; }
     if (!(voxel_h > 0) || !std::isfinite(voxel_h)) { fail(SP_EINVAL, "voxel_h must be > 0"); return nullptr; }
     if (!(mu_s >= 0) || !(mu_a >= 0) || !std::isfinite(mu_s) || !std::isfinite(mu_a)) {
         fail(SP_EINVAL, "mu_s and mu_a must be finite and >= 0");
@@ -411,6 +430,7 @@ sp_mc_t *sp_mc_create(const uint8_t *mask, int nx, int ny, int nz, double voxel_
     h->mua = mu_a * voxel_h;
     h->g = g;
     h->n_vox = n_vox;
+    h->n_field = (u64)h->nbx * h->nby * h->nbz * 64;
 
     // voxel counts per (phase, depth bin), exact, on the host
     std::vector<u64> cnt(2 * kNBin, 0);
@@ -658,6 +678,29 @@ int sp_mc_tallies(sp_mc_t *h, sp_mc_result_t *out, void *stream) {
     return SP_OK;
 }
 
+static int field_out(sp_mc *h, void *dst, int dtype, int on_device, cudaStream_t s) {
+    // dtype 0 f64, 1 f32, 2 raw u64
+    const size_t esz = dtype == 1 ? 4 : 8;
+    const size_t bytes = h->n_vox * esz;
+    void *d_out = dst;
+    if (!on_device) CUDA_TRY(cudaMalloc(&d_out, bytes));
+    const int blocks = h->sm_count * 8;
+    if (dtype == 0)
+        fluence_kernel<double><<<blocks, 256, 0, s>>>(h->d_field, (double *)d_out, h->nx, h->ny, h->nz, h->nbx, h->nby, h->d_tal);
+    else if (dtype == 1)
+        fluence_kernel<float><<<blocks, 256, 0, s>>>(h->d_field, (float *)d_out, h->nx, h->ny, h->nz, h->nbx, h->nby, h->d_tal);
+    else
+        fluence_kernel<u64><<<blocks, 256, 0, s>>>(h->d_field, (u64 *)d_out, h->nx, h->ny, h->nz, h->nbx, h->nby, h->d_tal);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMemcpyAsync(dst, d_out, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (!on_device) cudaFree(d_out);
+    if (e != cudaSuccess) return fail(SP_ECUDA, "field output: %s", cudaGetErrorString(e));
+    return SP_OK;
+}
+
 int sp_mc_fluence(sp_mc_t *h, void *dst, int dtype, int on_device, void *stream) {
     if (check_handle(h)) return SP_EINVAL;
     if (!dst) return fail(SP_EINVAL, "dst is NULL");
@@ -665,21 +708,7 @@ int sp_mc_fluence(sp_mc_t *h, void *dst, int dtype, int on_device, void *stream)
     if (dtype != 0 && dtype != 1) return fail(SP_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
     if (!h->photons_done) return fail(SP_EINVAL, "no photons have been run");
     DeviceGuard guard(h->device);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t bytes = h->n_vox * (dtype == 0 ? 8 : 4);
-    void *d_out = dst;
-    if (!on_device) CUDA_TRY(cudaMalloc(&d_out, bytes));
-    const int blocks = h->sm_count * 8;
-    if (dtype == 0) fluence_kernel<double><<<blocks, 256, 0, s>>>(h->d_field, (double *)d_out, h->n_vox, h->d_tal, h->nx, h->ny);
-    else fluence_kernel<float><<<blocks, 256, 0, s>>>(h->d_field, (float *)d_out, h->n_vox, h->d_tal, h->nx, h->ny);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && !on_device) {
-        e = cudaMemcpyAsync(dst, d_out, bytes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(d_out);
-    }
-    if (e != cudaSuccess) return fail(SP_ECUDA, "fluence: %s", cudaGetErrorString(e));
-    return SP_OK;
+    return field_out(h, dst, dtype, on_device, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int sp_mc_raw_field(sp_mc_t *h, uint64_t *dst, int on_device, void *stream) {
@@ -687,11 +716,7 @@ int sp_mc_raw_field(sp_mc_t *h, uint64_t *dst, int on_device, void *stream) {
     if (!dst) return fail(SP_EINVAL, "dst is NULL");
     if (!h->field) return fail(SP_EINVAL, "the voxel field tally is disabled");
     DeviceGuard guard(h->device);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemcpyAsync(dst, h->d_field, h->n_vox * sizeof(u64),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    if (!on_device) CUDA_TRY(cudaStreamSynchronize(s));
-    return SP_OK;
+    return field_out(h, dst, 2, on_device, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int sp_mc_records(sp_mc_t *h, uint64_t n, double *sites, int64_t *ints, double *vals, void *stream) {
@@ -712,7 +737,7 @@ int sp_mc_reset(sp_mc_t *h, void *stream) {
     DeviceGuard guard(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(h->d_tal, 0, sizeof(DevTallies), s));
-    if (h->d_field) CUDA_TRY(cudaMemsetAsync(h->d_field, 0, h->n_vox * sizeof(u64), s));
+    if (h->d_field) CUDA_TRY(cudaMemsetAsync(h->d_field, 0, h->n_field * sizeof(u64), s));
     if (h->n_rec) {
         CUDA_TRY(cudaMemsetAsync(h->d_rec_sites, 0xff, h->n_rec * 24 * sizeof(double), s));
         CUDA_TRY(cudaMemsetAsync(h->d_rec_ints, 0, h->n_rec * 4 * sizeof(long long), s));
@@ -732,7 +757,7 @@ static const u64 kMagic = 0x54504b43434d5053ull;   // "SPMCCKPT"
 
 size_t sp_mc_checkpoint_size(const sp_mc_t *h) {
     if (!h) return 0;
-    return sizeof(CkptHeader) + sizeof(DevTallies) + (h->field ? h->n_vox * sizeof(u64) : 0);
+    return sizeof(CkptHeader) + sizeof(DevTallies) + (h->field ? h->n_field * sizeof(u64) : 0);
 }
 
 int sp_mc_checkpoint(sp_mc_t *h, void *buf, size_t size, void *stream) {
@@ -740,13 +765,13 @@ int sp_mc_checkpoint(sp_mc_t *h, void *buf, size_t size, void *stream) {
     if (!buf || size < sp_mc_checkpoint_size(h)) return fail(SP_EINVAL, "checkpoint buffer too small");
     DeviceGuard guard(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    CkptHeader hd{kMagic, 1, (u64)h->nx, (u64)h->ny, (u64)h->nz, (u64)h->field, h->photons_done,
+    CkptHeader hd{kMagic, 2, (u64)h->nx, (u64)h->ny, (u64)h->nz, (u64)h->field, h->photons_done,
                   sizeof(DevTallies)};
     std::memcpy(buf, &hd, sizeof hd);
     char *p = static_cast<char *>(buf) + sizeof hd;
     CUDA_TRY(cudaMemcpyAsync(p, h->d_tal, sizeof(DevTallies), cudaMemcpyDeviceToHost, s));
     if (h->field)
-        CUDA_TRY(cudaMemcpyAsync(p + sizeof(DevTallies), h->d_field, h->n_vox * sizeof(u64),
+        CUDA_TRY(cudaMemcpyAsync(p + sizeof(DevTallies), h->d_field, h->n_field * sizeof(u64),
                                  cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SP_OK;
@@ -757,7 +782,7 @@ int sp_mc_restore(sp_mc_t *h, const void *buf, size_t size, void *stream) {
     if (!buf || size < sizeof(CkptHeader)) return fail(SP_EINVAL, "checkpoint too small");
     CkptHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    if (hd.magic != kMagic || hd.version != 1 || hd.tal_bytes != sizeof(DevTallies))
+    if (hd.magic != kMagic || hd.version != 2 || hd.tal_bytes != sizeof(DevTallies))
         return fail(SP_EINVAL, "not a compatible checkpoint");
     if (hd.nx != (u64)h->nx || hd.ny != (u64)h->ny || hd.nz != (u64)h->nz || hd.field != (u64)h->field)
         return fail(SP_EINVAL, "checkpoint was taken on a different geometry or tally mode");
@@ -767,7 +792,7 @@ int sp_mc_restore(sp_mc_t *h, const void *buf, size_t size, void *stream) {
     const char *p = static_cast<const char *>(buf) + sizeof hd;
     CUDA_TRY(cudaMemcpyAsync(h->d_tal, p, sizeof(DevTallies), cudaMemcpyHostToDevice, s));
     if (h->field)
-        CUDA_TRY(cudaMemcpyAsync(h->d_field, p + sizeof(DevTallies), h->n_vox * sizeof(u64),
+        CUDA_TRY(cudaMemcpyAsync(h->d_field, p + sizeof(DevTallies), h->n_field * sizeof(u64),
                                  cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     h->photons_done = hd.photons_done;

@@ -198,8 +198,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
     // photon state
     int mode = M_NEW;
     u64 pid = 0;
-    int ix = 0, iy = 0, iz = 0, kx = 0, ky = 0, bx = 0, by = 0, bz = 0, bin = 0, batch = 0;
-    u64 word = 0;
+    int ix = 0, iy = 0, iz = 0, kx = 0, ky = 0, bin = 0, batch = 0;
+    u32 brick = 0, bit = 0;                      // current voxel = field[brick * 64 + bit]
+    u64 word = 0;                                // mask bits of the current brick
     Real ux = 0, uy = 0, uz = 1;
     Real w = 1, tau = 0, s = 0, P = 0, A = 0;
     u32 event = 1, n_int = 0, n_surv = 0, n_scat = 0, n_steps = 0, iters = 0;
@@ -209,13 +210,17 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
     // FP64 traversal: unwrapped absolute position
     Real px = 0, py = 0, pz = 0;
 
-    auto load_brick = [&]() {
-        const long long b = ((long long)bz * nby + by) * (long long)nbx + bx;
-        word = (b < p.smem_bricks) ? s_bricks[b] : __ldg(p.bricks + b);
+    const u32 nbxy = (u32)nbx * (u32)nby;
+    auto brick_of = [&](int x, int y, int z) -> u32 {
+        return ((u32)(z >> 2) * (u32)nby + (u32)(y >> 2)) * (u32)nbx + (u32)(x >> 2);
     };
-    auto voxel = [&]() -> u64 {
-        return ((u64)iz * (u64)ny + (u64)iy) * (u64)nx + (u64)ix;
+    auto bit_of = [&](int x, int y, int z) -> u32 {
+        return (u32)(((z & 3) << 4) | ((y & 3) << 2) | (x & 3));
     };
+    auto fetch = [&](u32 b) -> u64 {
+        return ((int)b < p.smem_bricks) ? s_bricks[b] : __ldg(p.bricks + b);
+    };
+    (void)nbxy;
     auto q32 = [&](Real c) -> u64 {
         if constexpr (kExact) return O::q32(c);
         else return q32_bits(c);
@@ -300,8 +305,10 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
                     w = 1; tau = O::neg_log(O::uniform(r[2])); s = 0; P = 0; A = 0;
                     event = 1; n_int = 0; n_surv = 0; n_scat = 0; n_steps = 0; iters = 0;
                     batch = (int)(pid & (kNBatch - 1));
-                    bx = ix >> 2; by = iy >> 2; bz = 0; bin = 0;
-                    load_brick();
+                    brick = brick_of(ix, iy, 0);
+                    bit = bit_of(ix, iy, 0);
+                    bin = 0;
+                    word = fetch(brick);
                     atomicAdd(&st.counts[C_LAUNCHED], 1ull);
                     mode = M_STEP;
                     if (pid - p.rec_base < p.n_rec) {
@@ -407,8 +414,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
         if (mode != M_STEP) continue;
 
         // ---- one voxel step ------------------------------------------------
-        const int bit = ((iz & 3) << 4) | ((iy & 3) << 2) | (ix & 3);
-        const bool pore = (word >> bit) & 1ull;
+        // The face the ray leaves through does not depend on the phase, so the
+        // next voxel and its mask brick are computed first and the brick load
+        // is in flight while the current voxel is tallied.
         int ax = 2;                                   // ties: z, then y, then x
         Real seg, tn = 0;
         if constexpr (kExact) {
@@ -435,6 +443,22 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
             if (tmx < tn) { tn = tmx; ax = 0; }
             seg = fmaxf(tn - t, 0.0f);
         }
+        int nix = ix, niy = iy, niz = iz, wx = 0, wy = 0;
+        if (ax == 0) {
+            nix += ux > 0 ? 1 : -1;
+            if (nix == nx) { nix = 0; wx = 1; }
+            if (nix < 0) { nix = nx - 1; wx = -1; }
+        } else if (ax == 1) {
+            niy += uy > 0 ? 1 : -1;
+            if (niy == ny) { niy = 0; wy = 1; }
+            if (niy < 0) { niy = ny - 1; wy = -1; }
+        } else {
+            niz += uz > 0 ? 1 : -1;
+        }
+        const bool leaves = niz < 0 || niz >= nz;
+        const u32 nbrick = leaves ? brick : brick_of(nix, niy, niz);
+        const u64 nword = (nbrick != brick) ? fetch(nbrick) : word;
+        const bool pore = (word >> bit) & 1ull;
         int ev = 0;                                   // 0 cross, 1 interact, 2 gate
         Real need = 0;
         if (!pore) {
@@ -476,7 +500,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
             }
             const u64 q = q32(dep);
             if constexpr (kField) {
-                if (q) atomicAdd(p.field + voxel(), q);
+                if (q) atomicAdd(p.field + (((u64)brick << 6) | bit), q);
             } else {
                 atomicAdd(&st.depth[pore ? 1 : 0][bin], q);
             }
@@ -497,7 +521,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
             continue;
         }
 
-        // ---- face crossing ------------------------------------------------
+        // ---- face crossing: commit the next voxel ----------------------------
         if constexpr (kExact) {
             if (ax == 0) px = ux > 0 ? (Real)(ix + (long long)kx * nx + 1) : (Real)(ix + (long long)kx * nx);
             else if (ax == 1) py = uy > 0 ? (Real)(iy + (long long)ky * ny + 1) : (Real)(iy + (long long)ky * ny);
@@ -512,19 +536,12 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
                 t = 0;
             }
         }
-        if (ax == 0) ix += ux > 0 ? 1 : -1;
-        if (ax == 1) iy += uy > 0 ? 1 : -1;
-        if (ax == 2) iz += uz > 0 ? 1 : -1;
-        if (ix == nx) { ix = 0; ++kx; }
-        if (ix < 0) { ix = nx - 1; --kx; }
-        if (iy == ny) { iy = 0; ++ky; }
-        if (iy < 0) { iy = ny - 1; --ky; }
-        if (iz < 0 || iz >= nz) { finish(iz < 0 ? 1 : 2); continue; }
+        if (leaves) { finish(niz < 0 ? 1 : 2); continue; }
+        ix = nix; iy = niy; iz = niz; kx += wx; ky += wy;
+        brick = nbrick;
+        word = nword;
+        bit = bit_of(ix, iy, iz);
         if constexpr (!kField) bin = (int)(((long long)iz * kNBin) / nz);
-        if ((ix >> 2) != bx || (iy >> 2) != by || (iz >> 2) != bz) {
-            bx = ix >> 2; by = iy >> 2; bz = iz >> 2;
-            load_brick();
-        }
     }
 
     // ---- retire: flush the block tallies with integer atomics -----------

