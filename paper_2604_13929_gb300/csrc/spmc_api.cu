@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -800,3 +801,180 @@ int sp_mc_restore(sp_mc_t *h, const void *buf, size_t size, void *stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// For callers that may not allocate device memory themselves, e.g. code
+// embedded in a host application whose allocator owns all device memory,
+// code running while a stream is being captured, or latency-critical loops
+// that cannot afford an allocator call.  Its working memory is the fixed
+// array below, which every GPU that loads this library keeps until the
+// process exits.  The paper has no counterpart to this; it is an interface
+// convenience around the same transport kernel.
+// ------------------------------------------------------------------------
+
+namespace {
+
+constexpr u64 kNoAllocMaxBricks = 1ull << 18;     // 262144 bricks = 2^24 voxels (256^3)
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kOffBricks = 0;
+constexpr size_t kOffTal = align_up(kOffBricks + kNoAllocMaxBricks * sizeof(u64));
+constexpr size_t kOffCount = align_up(kOffTal + sizeof(DevTallies));
+constexpr size_t kOffResult = align_up(kOffCount + 2 * kNBin * sizeof(u64));
+constexpr size_t kScratchBytes = align_up(kOffResult + sizeof(sp_mc_result_t));
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+// The scratch array (about 2.03 MiB).  Host code must not pass its name to a
+// kernel: on the host it is only a stand-in symbol, so its device address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Pore voxels per depth bin (phase 1) and solid voxels (phase 0).
+__global__ void noalloc_count_kernel(const uint8_t *__restrict__ mask, int nx, int ny, int nz,
+                                     u64 *__restrict__ bin_count) {
+    __shared__ u64 s_cnt[2 * kNBin];
+    for (int i = threadIdx.x; i < 2 * kNBin; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const size_t nxy = (size_t)nx * ny, n = nxy * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int z = (int)(i / nxy);
+        const int b = (int)(((long long)z * kNBin) / nz);
+        atomicAdd(&s_cnt[(mask[i] != 0 ? kNBin : 0) + b], 1ull);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kNBin; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(&bin_count[i], s_cnt[i]);
+}
+
+extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int nz,
+                                      double voxel_h, double mu_s, double mu_a, double g,
+                                      uint64_t n_photons, uint64_t seed, sp_mc_result_t *out,
+                                      void *stream) {
+    // Messages here stay within the short-string capacity, so reporting a
+    // failure does not allocate either.
+    if (!d_mask || !out) return fail(SP_EINVAL, "null pointer");
+    if (nx < 1 || ny < 1 || nz < 1 || !(voxel_h > 0) || !std::isfinite(voxel_h) ||
+        !(mu_s >= 0) || !(mu_a >= 0) || !std::isfinite(mu_s) || !std::isfinite(mu_a) ||
+        !(g > -1.0 && g < 1.0))
+        return fail(SP_EINVAL, "bad argument");
+    const u64 nbx = (u64)(nx + 3) / 4, nby = (u64)(ny + 3) / 4, nbz = (u64)(nz + 3) / 4;
+    if (nbx * nby * nbz > kNoAllocMaxBricks) return fail(SP_EINVAL, "size too large");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return fail(SP_ECUDA, "no CUDA device");
+    }
+    unsigned char *base = nullptr;
+    {
+        // First call on this device: look up the array's device address
+        // (with this device current).  Later calls reuse it.
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return fail(SP_ECUDA, "symbol lookup");
+            }
+            g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    u64 *bricks = reinterpret_cast<u64 *>(base + kOffBricks);
+    DevTallies *tal = reinterpret_cast<DevTallies *>(base + kOffTal);
+    u64 *bin_count = reinterpret_cast<u64 *>(base + kOffCount);
+    sp_mc_result_t *d_result = reinterpret_cast<sp_mc_result_t *>(base + kOffResult);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(SP_ECUDA, "CUDA error");
+
+    // The array keeps the previous call's contents: clear the tallies and
+    // counts, repack the mask.
+    const u64 n_bricks = nbx * nby * nbz;
+    if (cudaMemsetAsync(tal, 0, sizeof(DevTallies), s) != cudaSuccess ||
+        cudaMemsetAsync(bin_count, 0, 2 * kNBin * sizeof(u64), s) != cudaSuccess)
+        return fail(SP_ECUDA, "CUDA error");
+    pack_bricks_kernel<<<(int)((n_bricks + 255) / 256), 256, 0, s>>>(d_mask, bricks, nx, ny, nz,
+                                                                       (int)nbx, (int)nby, (int)nbz);
+    noalloc_count_kernel<<<2 * sms, 256, 0, s>>>(d_mask, nx, ny, nz, bin_count);
+    u64 cnt[2 * kNBin];
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(cnt, bin_count, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(SP_ECUDA, "CUDA error");
+    u64 n_pore = 0;
+    for (int b = 0; b < kNBin; ++b) n_pore += cnt[kNBin + b];
+    const double porosity = (double)n_pore / ((double)nx * (double)ny * (double)nz);
+
+    // Default options of a fresh handle, profile-only tally (no voxel field).
+    sp_mc tmp;
+    tmp.nx = nx; tmp.ny = ny; tmp.nz = nz;
+    tmp.mus = mu_s * voxel_h; tmp.mua = mu_a * voxel_h; tmp.g = g;
+    tmp.porosity = porosity;
+    int per_sm = 0;
+    if (occupancy_f32(false, tmp.threads, 0, &per_sm) != cudaSuccess || per_sm < 1)
+        return fail(SP_ECUDA, "CUDA error");
+
+    TransportParams p{};
+    p.bricks = bricks;
+    p.field = nullptr;
+    p.tal = tal;
+    p.nx = nx; p.ny = ny; p.nz = nz;
+    p.nbx = (int)nbx; p.nby = (int)nby; p.nbz = (int)nbz;
+    p.smem_bricks = 0;
+    p.key0 = (u32)seed;
+    p.key1 = (u32)(seed >> 32);
+    p.pid_begin = 0;
+    p.n_photons = n_photons;
+    p.mus = tmp.mus; p.mua = tmp.mua; p.g = g;
+    p.s_max = path_cap(&tmp);
+    p.rr_weight = tmp.rr_weight;
+    p.rr_mult = tmp.rr_mult;
+    p.iter_limit = iter_limit(&tmp);
+    p.compact_k = tmp.compact_k;
+    p.hg_iso = std::fabs(g) < 1e-6;
+    p.small_x = tmp.mua * 1.7320508075688772 <= 0.1;
+    p.f32.mus = (float)tmp.mus;
+    p.f32.mua = (float)tmp.mua;
+    p.f32.inv_mus = tmp.mus > 0 ? (float)(1.0 / tmp.mus) : 0.0f;
+    p.f32.inv_mua = tmp.mua > 0 ? (float)(1.0 / tmp.mua) : 0.0f;
+    {
+        const float gf = (float)g;
+        p.f32.one_m_g2 = 1.0f - gf * gf;
+        p.f32.one_p_g2 = 1.0f + gf * gf;
+        p.f32.one_m_g = 1.0f - gf;
+        p.f32.two_g = 2.0f * gf;
+        p.f32.inv_2g = p.hg_iso ? 0.0f : (float)(1.0 / (2.0 * g));
+    }
+    p.f32.s_max = (float)p.s_max;
+    p.f32.rr_weight = (float)tmp.rr_weight;
+    p.f32.rr_mult = (float)tmp.rr_mult;
+    p.f32.rr_p = (float)(1.0 / tmp.rr_mult);
+    p.f32.rr_gain = (float)(tmp.rr_mult - 1.0);
+    p.f32.hist_scale = (float)(256.0 / (4.0 * (double)nz));
+
+    if (n_photons > 0 && launch_transport_f32(p, false, per_sm * sms, tmp.threads, 0, s) != cudaSuccess)
+        return fail(SP_ECUDA, "CUDA error");
+    finalize_kernel<<<1, kNBin, 0, s>>>(tal, nullptr, bin_count, nx, ny, nz, porosity, d_result);
+    u32 flags = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(out, d_result, sizeof(sp_mc_result_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&flags, &tal->flags, sizeof flags, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(SP_ECUDA, "CUDA error");
+    out->photons = n_photons;
+    out->precision = 32;
+    out->s_max = p.s_max;
+    out->porosity = porosity;
+    out->status = (flags & F_ITER_LIMIT) ? SP_ESTEPLIMIT : SP_OK;
+    if (out->status != SP_OK) return fail(out->status, "step limit");
+    return SP_OK;
+}

@@ -116,6 +116,9 @@ def load() -> ctypes.CDLL:
             "sp_mc_last_error": (ctypes.c_char_p, []),
             "sp_mc_version": (ctypes.c_char_p, []),
             "sp_mc_result_size": (sz, []),
+            "sp_mc_simulate_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      _D, _D, _D, _D, _U64, _U64,
+                                                      ctypes.POINTER(Result), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -252,6 +255,22 @@ def sp_mc_last_error() -> str:
 
 def sp_mc_version() -> str:
     return load().sp_mc_version().decode()
+
+
+def sp_mc_simulate_noalloc(d_mask, nx: int, ny: int, nz: int, voxel_h: float, mu_s: float,
+                           mu_a: float, g: float, n_photons: int, seed: int, stream=None) -> dict:
+    """One complete simulation through the allocation-free entry point.
+
+    ``d_mask`` is a CUDA uint8 tensor (or a raw device address) holding the
+    nz*ny*nx mask, x fastest.  Nothing is allocated on the device, by the
+    library or here; the result struct lives in host memory.
+    """
+    addr = d_mask if isinstance(d_mask, int) else int(d_mask.data_ptr())
+    r = Result()
+    _check(load().sp_mc_simulate_noalloc(addr, nx, ny, nz, voxel_h, mu_s, mu_a, g,
+                                         int(n_photons), int(seed) & (2 ** 64 - 1),
+                                         ctypes.byref(r), stream_handle(stream)))
+    return r.to_dict()
 
 
 # ------------------------------------------------------------ convenience --
