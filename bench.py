@@ -41,6 +41,17 @@ WORKLOAD = ("256^3 Cahn-Hilliard spinodal mask (dt 0.1, 4000 steps, seed 0), por
 # a voxel step, an interaction event and a photon launch.
 OPS_STEP, OPS_INTERACT, OPS_LAUNCH = 30, 120, 90
 ISSUE_PER_SM_CLK = 4          # warp instructions per SM per clock (4 schedulers)
+# DRAM bytes (read + write) per photon of the transport kernel from one ncu capture
+# (2e7 photons of this workload), valid only for the kernel source it was taken on.
+TRAFFIC_CAPTURE = {"kernel_sha256_prefix": "908996d35b57c202", "dram_bytes_per_photon": 15961.5,
+                   "source": "profiles/transport_kernel_256cubed_phi090.md"}
+
+
+def _kernel_sha_prefix():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2604_13929_gb300", "csrc", "spmc_transport.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def _env_int(name, default):
@@ -105,10 +116,15 @@ def cpu_baseline(mask, target_s=15.0):
     """The FP64 oracle, as it stands, on all host cores over a bounded sample."""
     from oracle import oracle as orc
     cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    r = orc.run(mask, MUS, MUA, G, 2000, SEED, n_threads=cores, field=True)
-    dt = time.perf_counter() - t0
-    n = int(min(max(2000 * target_s / max(dt, 1e-3), 2000), 5_000_000))
+    n = 2000
+    while True:                      # calibrate on samples of at least ~1 s
+        t0 = time.perf_counter()
+        orc.run(mask, MUS, MUA, G, n, SEED, n_threads=cores, field=True)
+        dt = time.perf_counter() - t0
+        if dt > 1.0 or n >= 5_000_000:
+            break
+        n *= 4
+    n = int(min(max(n * target_s / max(dt, 1e-3), 2000), 20_000_000))
     t0 = time.perf_counter()
     r = orc.run(mask, MUS, MUA, G, n, SEED, n_threads=cores, field=True)
     dt = time.perf_counter() - t0
@@ -158,6 +174,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
+                    help="profiling case: one warm-up launch of N/10 photons, then one timed "
+                         "launch of N photons on the workload; prints its time and exits")
     args = ap.parse_args()
 
     rank = _env_int("RANK", 0)
@@ -183,6 +202,20 @@ def main():
 
     mask = make_mask("cuda")
     stream = torch.cuda.current_stream()
+    if args.profile_launch:
+        prof = spmc.Simulation(mask, MUS, MUA, G)
+        prof.run(max(args.profile_launch // 10, 1), SEED + 1, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prof.run(args.profile_launch, SEED, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = prof.tallies(stream)
+        print(json.dumps({"profile_launch_photons": args.profile_launch,
+                          "ms": e0.elapsed_time(e1), "steps": t["steps"],
+                          "interactions": t["interactions"]}), flush=True)
+        prof.close()
+        return
     seed = SEED + rank                      # replicas: independent photon streams per rank
     sim = spmc.Simulation(mask, MUS, MUA, G)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
@@ -239,14 +272,29 @@ def main():
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak = props.multi_processor_count * ISSUE_PER_SM_CLK * max_mhz * 1e6
     achieved = ops / (launch_ms / 1e3)
+    traffic = None
+    if _kernel_sha_prefix() == TRAFFIC_CAPTURE["kernel_sha256_prefix"]:
+        traffic = TRAFFIC_CAPTURE["dram_bytes_per_photon"] * args.photons
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "DRAM read+write bytes per launch, ncu capture of 2e7 photons "
+                                "scaled by the photon count (null if the kernel changed since)",
                 "kernel": "spmc::transport_kernel<float,true>",
                 "peak_source": f"{props.multi_processor_count} SMs x {ISSUE_PER_SM_CLK} "
                                f"warp-inst/clk x {max_mhz:.0f} MHz (max SM clock)",
                 "launch_ms": launch_ms,
                 "frac_at_measured_clock": (achieved / (peak * clocks["sm_mhz"] / max_mhz)
                                            if clocks["sm_mhz"] else None)}
+
+    # measured ceiling of the step pattern: straight rays through an all-pore
+    # 256^3 volume, with and without one Q32.32 RED per step into a 256^3 field
+    ceil_red = spmc.sp_mc_probe_step_ceiling(N_VOX, True)["steps_per_s"]
+    ceil_nored = spmc.sp_mc_probe_step_ceiling(N_VOX, False)["steps_per_s"]
+    roofline["step_ceiling"] = {
+        "with_field_red_steps_per_s": ceil_red, "without_red_steps_per_s": ceil_nored,
+        "frac_of_red_ceiling": value * steps_per_photon / ceil_red,
+        "note": "sp_mc_probe_step_ceiling: the kernel's traversal and tally memory pattern "
+                "with no physics; the 256^3 Q32.32 field (134 MB) exceeds L2"}
 
     # end to end through the C ABI with host buffers: upload + pack the host
     # mask, transport, normalise, copy the results back

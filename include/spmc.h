@@ -197,6 +197,19 @@ const char *sp_mc_last_error(void);
 /* Library version, e.g. "spmc 0.1.0 sm_103a". */
 const char *sp_mc_version(void);
 
+/*
+ * Measurement helper with no counterpart in the paper: the throughput ceiling
+ * of the transport kernel's memory pattern on this GPU.  Straight rays step
+ * face by face through an all-pore n^3 volume (n a power of two in
+ * [16, 1024]) with the transport kernel's traversal arithmetic and mask-brick
+ * fetches, and, when red != 0, one Q32.32 RED.ADD.U64 per step into an n^3
+ * brick-layout field (8 n^3 bytes, allocated and freed by the call).  One
+ * timed launch of steps_per_thread steps per thread on the current device;
+ * *ms gets its CUDA-event time and *steps_per_s the step rate.
+ */
+int sp_mc_probe_step_ceiling(int n, int red, long long steps_per_thread, double *ms,
+                             double *steps_per_s);
+
 /* sizeof(sp_mc_result_t) as compiled into the library, so bindings can
  * verify their copy of the layout. */
 size_t sp_mc_result_size(void);

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libspmc.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["spmc_api.cu", "spmc_transport_f32.cu", "spmc_transport_f64.cu"]
+SOURCES = ["spmc_api.cu", "spmc_transport_f32.cu", "spmc_transport_f64.cu", "spmc_probe.cu"]
 # The FP64 transport evaluates the plain-definition formulas in their written
 # order; contraction into fused multiply-adds would change its rounding.
 PER_SOURCE_FLAGS = {"spmc_transport_f64.cu": ["-fmad=false"]}

@@ -115,16 +115,20 @@ struct SmemTallies {
     u64 depth[2][kNBin];
 };
 
-// Q32.32 quantisation of a float 0 <= c < 2^31 with integer operations only
-// (round to nearest, ties up): c = m 2^(e-23) with a 24-bit significand m, so
-// c 2^32 = m 2^(e+9).  Values below 2^-33 round to zero.
+// Q32.32 quantisation, round to nearest even, of a float 0 <= c < 2^13, with
+// FP32 arithmetic only (no conversion instruction, no branch).  c is split
+// exactly into k1 2^-9 + r with integer k1 = rint(c 2^9) and |r| <= 2^-10,
+// each part rounded by adding 1.5 2^23 (the sum's low mantissa bits are then
+// the rounded integer): c 2^32 = k1 2^23 + r 2^32, and rint(r 2^32) rounds
+// only the fraction, so q = k1 2^23 + rint(r 2^32) = rint(c 2^32).
 __device__ __forceinline__ u64 q32_bits(float c) {
-    const u32 b = __float_as_uint(c);
-    const int sh = (int)(b >> 23) - 118;            // e + 9 with e = exponent - 127
-    const u64 m = (u64)((b & 0x7fffffu) | 0x800000u);
-    if (sh >= 0) return m << sh;
-    if (sh < -25) return 0ull;
-    return (m + (1ull << (-sh - 1))) >> (-sh);
+    const float magic = 12582912.0f;                       // 1.5 * 2^23
+    const float t1 = fmaf(c, 512.0f, magic);               // k1 in the low bits
+    const int k1 = (int)(__float_as_uint(t1) - 0x4B400000u);
+    const float r = fmaf(t1 - magic, -1.0f / 512.0f, c);   // exact remainder
+    const float t2 = fmaf(r, 4294967296.0f, magic);        // |r 2^32| <= 2^22
+    const int k2 = (int)(__float_as_uint(t2) - 0x4B400000u);
+    return ((u64)(u32)k1 << 23) + (u64)(long long)k2;
 }
 
 // Lane modes of the persistent loop.
@@ -149,8 +153,18 @@ enum { M_STEP = 0, M_EVENT = 1, M_NEW = 2, M_DONE = 3 };
 // runs the Philox block and the event code for all parked lanes at once.
 // Each photon's history depends only on its id, so the order of events
 // across lanes changes nothing in the results.
+// Launch-shape tuning knobs (compile time): voxel steps per pass of the
+// warp-level event check, and the minimum resident CTAs per SM requested
+// from the register allocator.
+#ifndef SPMC_STEPS_PER_PASS
+#define SPMC_STEPS_PER_PASS 1
+#endif
+#ifndef SPMC_MIN_BLOCKS
+#define SPMC_MIN_BLOCKS 1
+#endif
+
 template <typename Real, bool kField>
-__global__ void __launch_bounds__(256) transport_kernel(const TransportParams p) {
+__global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const TransportParams p) {
     using O = Ops<Real>;
     constexpr bool kExact = sizeof(Real) == 8;
     extern __shared__ u64 s_bricks[];
@@ -199,6 +213,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
     int mode = M_NEW;
     u64 pid = 0;
     int ix = 0, iy = 0, iz = 0, kx = 0, ky = 0, bin = 0, batch = 0;
+    int sx = 1, sy = 1, sz = 1;                  // step direction per axis along the ray
     u32 brick = 0, bit = 0;                      // current voxel = field[brick * 64 + bit]
     u64 word = 0;                                // mask bits of the current brick
     Real ux = 0, uy = 0, uz = 1;
@@ -260,6 +275,135 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
         mode = M_NEW;
     };
 
+    // ---- one voxel step of a lane in M_STEP ------------------------------
+    auto step = [&]() {
+        // ---- one voxel step ------------------------------------------------
+        // The face the ray leaves through does not depend on the phase, so the
+        // next voxel and its mask brick are computed first and the brick load
+        // is in flight while the current voxel is tallied.
+        int ax = 2;                                   // ties: z, then y, then x
+        Real seg, tn = 0;
+        if constexpr (kExact) {
+            const long long jx = ix + (long long)kx * nx, jy = iy + (long long)ky * ny;
+            Real d0, d1, d2;
+            if (ux > 0) d0 = ((Real)(jx + 1) - px) / ux;
+            else if (ux < 0) d0 = ((Real)jx - px) / ux;
+            else d0 = kInf;
+            if (uy > 0) d1 = ((Real)(jy + 1) - py) / uy;
+            else if (uy < 0) d1 = ((Real)jy - py) / uy;
+            else d1 = kInf;
+            if (uz > 0) d2 = ((Real)(iz + 1) - pz) / uz;
+            else if (uz < 0) d2 = ((Real)iz - pz) / uz;
+            else d2 = kInf;
+            if (d0 < 0) d0 = 0;
+            if (d1 < 0) d1 = 0;
+            if (d2 < 0) d2 = 0;
+            seg = d2;
+            if (d1 < seg) { seg = d1; ax = 1; }
+            if (d0 < seg) { seg = d0; ax = 0; }
+        } else {
+            tn = tmz;
+            if (tmy < tn) { tn = tmy; ax = 1; }
+            if (tmx < tn) { tn = tmx; ax = 0; }
+            seg = fmaxf(tn - t, 0.0f);
+        }
+        // next voxel, branch-free: step the crossed axis, wrap x and y
+        int nix = ix + (ax == 0 ? sx : 0);
+        int niy = iy + (ax == 1 ? sy : 0);
+        const int niz = iz + (ax == 2 ? sz : 0);
+        const int wx = (nix >= nx) - (nix < 0), wy = (niy >= ny) - (niy < 0);
+        nix = wx > 0 ? 0 : (wx < 0 ? nx - 1 : nix);
+        niy = wy > 0 ? 0 : (wy < 0 ? ny - 1 : niy);
+        const bool leaves = niz < 0 || niz >= nz;
+        const u32 nbrick = leaves ? brick : brick_of(nix, niy, niz);
+        const u64 nword = (nbrick != brick) ? fetch(nbrick) : word;
+        const bool pore = (word >> bit) & 1ull;
+        int ev = 0;                                   // 0 cross, 1 interact, 2 gate
+        Real need = 0;
+        if (!pore) {
+            need = mus * seg;                         // tau > 0, so mu_s = 0 never interacts
+            if (tau < need) {
+                if constexpr (kExact) seg = tau / mus;
+                else seg = tau * inv_mus;
+                ev = 1;
+            }
+        }
+        if (!(s + seg < s_max)) {                     // NaN-safe: a NaN path is gated
+            seg = s_max - s;
+            if (!(seg > 0)) seg = 0;
+            ev = 2;
+        }
+        if (++iters > iter_limit) { ev = 2; atomicOr(&p.tal->flags, (u32)F_ITER_LIMIT); }
+
+        if (seg > 0) {
+            Real dep;
+            if (pore) {
+                dep = w * seg;
+                P += seg;
+            } else if (absorb_on) {
+                const Real x = mua * seg;
+                if constexpr (kExact) {
+                    const Real f = O::one_minus_exp(x);
+                    dep = w * f / mua;
+                    A += w * f;
+                    w = w * exp(-x);
+                } else {
+                    const Real f = small_x ? O::one_minus_exp_small(x) : O::one_minus_exp(x);
+                    const Real dA = w * f;
+                    dep = dA * inv_mua;
+                    A += dA;
+                    w = w - dA;
+                }
+            } else {
+                dep = w * seg;
+            }
+            const u64 q = q32(dep);
+            if constexpr (kField) {
+                if (q) atomicAdd(p.field + (((u64)brick << 6) | bit), q);
+            } else {
+                atomicAdd(&st.depth[pore ? 1 : 0][bin], q);
+            }
+            s += seg;
+            ++n_steps;
+        }
+        if (ev == 0) tau -= need;
+        if constexpr (kExact) {
+            px += seg * ux;
+            py += seg * uy;
+            pz += seg * uz;
+        }
+
+        if (ev == 2) { finish(4); return; }
+        if (ev == 1) {
+            if constexpr (!kExact) t += seg;
+            mode = M_EVENT;
+            return;
+        }
+
+        // ---- face crossing: commit the next voxel ----------------------------
+        if constexpr (kExact) {
+            if (ax == 0) px = ux > 0 ? (Real)(ix + (long long)kx * nx + 1) : (Real)(ix + (long long)kx * nx);
+            else if (ax == 1) py = uy > 0 ? (Real)(iy + (long long)ky * ny + 1) : (Real)(iy + (long long)ky * ny);
+            else pz = uz > 0 ? (Real)(iz + 1) : (Real)iz;
+        } else {
+            t = tn;
+            if (ax == 0) tmx += dtx;
+            if (ax == 1) tmy += dty;
+            if (ax == 2) tmz += dtz;
+            if (t > 4.0f) {             // rebase the ray parameters at the current point
+                tmx -= t; tmy -= t; tmz -= t;
+                t = 0;
+            }
+        }
+        if (leaves) { finish(niz < 0 ? 1 : 2); return; }
+        ix = nix; iy = niy; iz = niz; kx += wx; ky += wy;
+        brick = nbrick;
+        word = nword;
+        bit = bit_of(ix, iy, iz);
+        if constexpr (!kField) bin = (int)(((long long)iz * kNBin) / nz);
+    };
+
+
     for (;;) {
         // ---- event phase: claims, launches and interactions, compacted ---
         const unsigned parked = __ballot_sync(kFull, mode == M_EVENT || mode == M_NEW);
@@ -296,6 +440,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
                     iz = 0;
                     kx = ky = 0;
                     ux = 0; uy = 0; uz = 1;
+                    sx = 1; sy = 1; sz = 1;
                     if constexpr (kExact) {
                         px = xr; py = yr; pz = 0;
                     } else {
@@ -394,6 +539,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
                         }
                         tau = O::neg_log(O::uniform(r[2]));
                         ++n_scat;
+                        sx = ux > 0 ? 1 : -1;
+                        sy = uy > 0 ? 1 : -1;
+                        sz = uz > 0 ? 1 : -1;
                         if constexpr (!kExact) {   // new ray from (fx, fy, fz)
                             if (ux > 0)      { dtx = O::rcp(ux);  tmx = (1.0f - fx) * dtx; }
                             else if (ux < 0) { dtx = O::rcp(-ux); tmx = fx * dtx; }
@@ -412,136 +560,11 @@ __global__ void __launch_bounds__(256) transport_kernel(const TransportParams p)
             }
         }
         if (mode != M_STEP) continue;
-
-        // ---- one voxel step ------------------------------------------------
-        // The face the ray leaves through does not depend on the phase, so the
-        // next voxel and its mask brick are computed first and the brick load
-        // is in flight while the current voxel is tallied.
-        int ax = 2;                                   // ties: z, then y, then x
-        Real seg, tn = 0;
-        if constexpr (kExact) {
-            const long long jx = ix + (long long)kx * nx, jy = iy + (long long)ky * ny;
-            Real d0, d1, d2;
-            if (ux > 0) d0 = ((Real)(jx + 1) - px) / ux;
-            else if (ux < 0) d0 = ((Real)jx - px) / ux;
-            else d0 = kInf;
-            if (uy > 0) d1 = ((Real)(jy + 1) - py) / uy;
-            else if (uy < 0) d1 = ((Real)jy - py) / uy;
-            else d1 = kInf;
-            if (uz > 0) d2 = ((Real)(iz + 1) - pz) / uz;
-            else if (uz < 0) d2 = ((Real)iz - pz) / uz;
-            else d2 = kInf;
-            if (d0 < 0) d0 = 0;
-            if (d1 < 0) d1 = 0;
-            if (d2 < 0) d2 = 0;
-            seg = d2;
-            if (d1 < seg) { seg = d1; ax = 1; }
-            if (d0 < seg) { seg = d0; ax = 0; }
-        } else {
-            tn = tmz;
-            if (tmy < tn) { tn = tmy; ax = 1; }
-            if (tmx < tn) { tn = tmx; ax = 0; }
-            seg = fmaxf(tn - t, 0.0f);
+#pragma unroll 1
+        for (int k = 0; k < SPMC_STEPS_PER_PASS; ++k) {   // voxel steps per pass of
+            if (mode != M_STEP) break;                     // the warp-level event check
+            step();
         }
-        int nix = ix, niy = iy, niz = iz, wx = 0, wy = 0;
-        if (ax == 0) {
-            nix += ux > 0 ? 1 : -1;
-            if (nix == nx) { nix = 0; wx = 1; }
-            if (nix < 0) { nix = nx - 1; wx = -1; }
-        } else if (ax == 1) {
-            niy += uy > 0 ? 1 : -1;
-            if (niy == ny) { niy = 0; wy = 1; }
-            if (niy < 0) { niy = ny - 1; wy = -1; }
-        } else {
-            niz += uz > 0 ? 1 : -1;
-        }
-        const bool leaves = niz < 0 || niz >= nz;
-        const u32 nbrick = leaves ? brick : brick_of(nix, niy, niz);
-        const u64 nword = (nbrick != brick) ? fetch(nbrick) : word;
-        const bool pore = (word >> bit) & 1ull;
-        int ev = 0;                                   // 0 cross, 1 interact, 2 gate
-        Real need = 0;
-        if (!pore) {
-            need = mus * seg;                         // tau > 0, so mu_s = 0 never interacts
-            if (tau < need) {
-                if constexpr (kExact) seg = tau / mus;
-                else seg = tau * inv_mus;
-                ev = 1;
-            }
-        }
-        if (!(s + seg < s_max)) {                     // NaN-safe: a NaN path is gated
-            seg = s_max - s;
-            if (!(seg > 0)) seg = 0;
-            ev = 2;
-        }
-        if (++iters > iter_limit) { ev = 2; atomicOr(&p.tal->flags, (u32)F_ITER_LIMIT); }
-
-        if (seg > 0) {
-            Real dep;
-            if (pore) {
-                dep = w * seg;
-                P += seg;
-            } else if (absorb_on) {
-                const Real x = mua * seg;
-                if constexpr (kExact) {
-                    const Real f = O::one_minus_exp(x);
-                    dep = w * f / mua;
-                    A += w * f;
-                    w = w * exp(-x);
-                } else {
-                    const Real f = small_x ? O::one_minus_exp_small(x) : O::one_minus_exp(x);
-                    const Real dA = w * f;
-                    dep = dA * inv_mua;
-                    A += dA;
-                    w = w - dA;
-                }
-            } else {
-                dep = w * seg;
-            }
-            const u64 q = q32(dep);
-            if constexpr (kField) {
-                if (q) atomicAdd(p.field + (((u64)brick << 6) | bit), q);
-            } else {
-                atomicAdd(&st.depth[pore ? 1 : 0][bin], q);
-            }
-            s += seg;
-            ++n_steps;
-        }
-        if (ev == 0) tau -= need;
-        if constexpr (kExact) {
-            px += seg * ux;
-            py += seg * uy;
-            pz += seg * uz;
-        }
-
-        if (ev == 2) { finish(4); continue; }
-        if (ev == 1) {
-            if constexpr (!kExact) t += seg;
-            mode = M_EVENT;
-            continue;
-        }
-
-        // ---- face crossing: commit the next voxel ----------------------------
-        if constexpr (kExact) {
-            if (ax == 0) px = ux > 0 ? (Real)(ix + (long long)kx * nx + 1) : (Real)(ix + (long long)kx * nx);
-            else if (ax == 1) py = uy > 0 ? (Real)(iy + (long long)ky * ny + 1) : (Real)(iy + (long long)ky * ny);
-            else pz = uz > 0 ? (Real)(iz + 1) : (Real)iz;
-        } else {
-            t = tn;
-            if (ax == 0) tmx += dtx;
-            if (ax == 1) tmy += dty;
-            if (ax == 2) tmz += dtz;
-            if (t > 4.0f) {             // rebase the ray parameters at the current point
-                tmx -= t; tmy -= t; tmz -= t;
-                t = 0;
-            }
-        }
-        if (leaves) { finish(niz < 0 ? 1 : 2); continue; }
-        ix = nix; iy = niy; iz = niz; kx += wx; ky += wy;
-        brick = nbrick;
-        word = nword;
-        bit = bit_of(ix, iy, iz);
-        if constexpr (!kField) bin = (int)(((long long)iz * kNBin) / nz);
     }
 
     // ---- retire: flush the block tallies with integer atomics -----------

@@ -116,6 +116,9 @@ def load() -> ctypes.CDLL:
             "sp_mc_last_error": (ctypes.c_char_p, []),
             "sp_mc_version": (ctypes.c_char_p, []),
             "sp_mc_result_size": (sz, []),
+            "sp_mc_probe_step_ceiling": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                                        ctypes.c_longlong,
+                                                        ctypes.POINTER(_D), ctypes.POINTER(_D)]),
             "sp_mc_simulate_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       _D, _D, _D, _D, _U64, _U64,
                                                       ctypes.POINTER(Result), vp]),
@@ -255,6 +258,14 @@ def sp_mc_last_error() -> str:
 
 def sp_mc_version() -> str:
     return load().sp_mc_version().decode()
+
+
+def sp_mc_probe_step_ceiling(n: int, red: bool, steps_per_thread: int = 20000) -> dict:
+    """Measured stepping ceiling (steps/s) of the transport's memory pattern."""
+    ms, rate = _D(), _D()
+    _check(load().sp_mc_probe_step_ceiling(int(n), 1 if red else 0, int(steps_per_thread),
+                                           ctypes.byref(ms), ctypes.byref(rate)))
+    return {"ms": ms.value, "steps_per_s": rate.value}
 
 
 def sp_mc_simulate_noalloc(d_mask, nx: int, ny: int, nz: int, voxel_h: float, mu_s: float,
