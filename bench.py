@@ -164,6 +164,65 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
+    """64 masks of uneven size and optics, 1e7 photons each, one persistent
+    launch per step (CUDA-graph replay), launch shape picked by the autotuner."""
+    from paper_2604_13929_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    problems = inputs.batch_workload(64, device="cuda")
+    gen_s = time.perf_counter() - t0
+    n_each = 10_000_000
+    b = spmc.Batch(problems)
+    tuned = b.autotune([n_each // 50] * len(problems), SEED + 7, stream)
+    for _ in range(args.warmup):
+        b.run([n_each] * len(problems), SEED + rank, stream)
+    torch.cuda.synchronize()
+    b.reset(stream)
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            b.run([n_each] * len(problems), SEED + rank, stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = start.elapsed_time(stop)
+    steps = sum(b.tallies(i, stream)["steps"] for i in range(len(problems)))
+    photons = n_each * len(problems) * args.steps * world
+    # the same problems one launch at a time (sp_mc_run per mask), for comparison
+    sims = [spmc.Simulation(m, mus, mua, g) for (m, mus, mua, g) in problems]
+    for sim in sims:
+        sim.run(n_each // 10, SEED, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sim in sims:
+        sim.run(n_each, SEED + rank, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_rate = n_each * len(problems) / (e0.elapsed_time(e1) / 1e3)
+    for sim in sims:
+        sim.close()
+    line = {"metric": "photons/s, batched (64 masks 64^3-256^3)", "value": photons / (ms / 1e3),
+            "unit": "photons/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 Cahn-Hilliard masks (1000 FP32 steps) of sizes "
+                                   "64^3..256^3, porosity U[0.5,0.95], mu_s h logU[0.1,2], "
+                                   "mu_a h U[0.001,0.05], g U[0,0.9]; 1e7 photons each per step; "
+                                   "one persistent launch per step, CUDA graph replay",
+                       "launch": {k: b.get_option(k) for k in ("threads", "blocks", "compact")},
+                       "autotune_photons_per_s": tuned, "mask_generation_s": gen_s},
+            "voxel_steps_per_s": steps * world / (ms / 1e3),
+            "sequential_photons_per_s": seq_rate,
+            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,6 +233,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch"],
+                    help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
+                         "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
     ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
                     help="profiling case: one warm-up launch of N/10 photons, then one timed "
                          "launch of N photons on the workload; prints its time and exits")
@@ -200,6 +262,9 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.workload == "batch":
+        batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier)
+        return
     mask = make_mask("cuda")
     stream = torch.cuda.current_stream()
     if args.profile_launch:

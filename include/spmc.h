@@ -72,9 +72,12 @@ enum sp_option {
                                 lets ranks run disjoint id ranges whose
                                 integer tallies sum to one larger run.
                                 Only before the first run.                */
-    SP_OPT_COMPACT     = 12  /* warp compaction threshold in [1, 32]: lanes
+    SP_OPT_COMPACT     = 12, /* warp compaction threshold in [1, 32]: lanes
                                 needing an interaction or a new photon wait
                                 until this many of their warp do (8)      */
+    SP_OPT_GRAPH       = 13  /* batched launches only: 1 (default) captures
+                                the launch in a CUDA graph and replays it
+                                while photon counts and seed are unchanged */
 };
 
 typedef struct sp_mc sp_mc_t;   /* opaque, owned by the library */
@@ -213,6 +216,49 @@ int sp_mc_probe_step_ceiling(int n, int red, long long steps_per_thread, double 
 /* sizeof(sp_mc_result_t) as compiled into the library, so bindings can
  * verify their copy of the layout. */
 size_t sp_mc_result_size(void);
+
+/* ---------------------------------------------------------- batches --- */
+/*
+ * Many masks of uneven size and optics transported in ONE persistent launch
+ * (the batched pattern of the design sweeps; the paper runs its cases one at
+ * a time).  Each problem has its own bit-packed mask, Q32.32 voxel field and
+ * integer tallies, exactly as an sp_mc_create handle; photons of all problems
+ * are claimed from one counter, so lanes carry photons of different problems.
+ * With the same seed and photon counts every problem's tallies equal those of
+ * a separate sp_mc_run on its own handle, bit for bit.
+ */
+typedef struct sp_mc_batch sp_mc_batch_t;
+
+/* masks[i]: host pointer to problem i's mask (as sp_mc_create);
+ * dims[3i..3i+2] = nx, ny, nz; optics[4i..4i+3] = voxel_h, mu_s, mu_a, g.
+ * Returns NULL on failure (sp_mc_last_error names the problem). */
+sp_mc_batch_t *sp_mc_batch_create(int n, const uint8_t *const *masks, const int *dims,
+                                  const double *optics);
+/* SP_OPT_THREADS (threads per CTA, default 128), SP_OPT_BLOCKS (CTAs per SM,
+ * 0 = as many as fit), SP_OPT_COMPACT, SP_OPT_GRAPH apply to the launch; the
+ * path-cap, roulette and iteration-limit options apply to every problem;
+ * tally mode, precision, records and photon-id offset are fixed (field,
+ * FP32, none, 0). */
+int sp_mc_batch_set_option(sp_mc_batch_t *b, int key, double value);
+int sp_mc_batch_get_option(const sp_mc_batch_t *b, int key, double *value);
+/* Run n_photons[i] photons of every problem i in one launch on `stream`;
+ * tallies accumulate and photon ids continue per problem as in sp_mc_run.
+ * With SP_OPT_GRAPH the first run of a given (n_photons, seed, launch shape)
+ * is captured as a CUDA graph {counter reset, transport, id advance} and
+ * later runs replay it. */
+int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed, void *stream);
+/* Results / raw field of problem i (as sp_mc_tallies / sp_mc_raw_field). */
+int sp_mc_batch_tallies(sp_mc_batch_t *b, int i, sp_mc_result_t *out, void *stream);
+int sp_mc_batch_raw_field(sp_mc_batch_t *b, int i, uint64_t *dst, int on_device, void *stream);
+/* Zero every problem's tallies and photon counter. */
+int sp_mc_batch_reset(sp_mc_batch_t *b, void *stream);
+/* Autotuner: times one batched run of n_photons[] for each candidate launch
+ * shape (threads per CTA 64/128/256, all or half the resident CTAs per SM,
+ * compaction threshold 4/8/12/16), keeps the fastest, stores its rate in
+ * *photons_per_s (may be NULL), then resets the tallies. */
+int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed,
+                         double *photons_per_s, void *stream);
+void sp_mc_batch_destroy(sp_mc_batch_t *b);
 
 /*
  * One complete simulation that allocates nothing.  The paper has no

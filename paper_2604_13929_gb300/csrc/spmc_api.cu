@@ -102,6 +102,30 @@ static u64 iter_limit(const sp_mc *h) {
     return lim > 4.0e9 ? 0xffffffffull : (u64)lim;
 }
 
+// FP32 copies of the optics and limits of a launch (computed on the host so
+// FP32 kernels never convert doubles inside their loop).
+static void fill_f32(const sp_mc *h, double s_max, TransportParams::F32 &f, int &hg_iso,
+                     int &small_x) {
+    hg_iso = std::fabs(h->g) < 1e-6;
+    small_x = h->mua * 1.7320508075688772 <= 0.1;
+    f.mus = (float)h->mus;
+    f.mua = (float)h->mua;
+    f.inv_mus = h->mus > 0 ? (float)(1.0 / h->mus) : 0.0f;
+    f.inv_mua = h->mua > 0 ? (float)(1.0 / h->mua) : 0.0f;
+    const float gf = (float)h->g;           // the FP32 kernel's g, expressions in FP32
+    f.one_m_g2 = 1.0f - gf * gf;
+    f.one_p_g2 = 1.0f + gf * gf;
+    f.one_m_g = 1.0f - gf;
+    f.two_g = 2.0f * gf;
+    f.inv_2g = hg_iso ? 0.0f : (float)(1.0 / (2.0 * h->g));
+    f.s_max = (float)s_max;
+    f.rr_weight = (float)h->rr_weight;
+    f.rr_mult = (float)h->rr_mult;
+    f.rr_p = (float)(1.0 / h->rr_mult);
+    f.rr_gain = (float)(h->rr_mult - 1.0);
+    f.hist_scale = (float)(256.0 / (4.0 * (double)h->nz));
+}
+
 // --------------------------------------------------------- kernels ------
 
 // One thread per 4x4x4 brick: bit (lz*4+ly)*4+lx set for pore voxels;
@@ -621,26 +645,7 @@ int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
     p.rr_mult = h->rr_mult;
     p.iter_limit = iter_limit(h);
     p.compact_k = h->compact_k;
-    p.hg_iso = std::fabs(h->g) < 1e-6;
-    p.small_x = h->mua * 1.7320508075688772 <= 0.1;
-    p.f32.mus = (float)h->mus;
-    p.f32.mua = (float)h->mua;
-    p.f32.inv_mus = h->mus > 0 ? (float)(1.0 / h->mus) : 0.0f;
-    p.f32.inv_mua = h->mua > 0 ? (float)(1.0 / h->mua) : 0.0f;
-    {
-        const float gf = (float)h->g;       // the FP32 kernel's g, and expressions in FP32
-        p.f32.one_m_g2 = 1.0f - gf * gf;
-        p.f32.one_p_g2 = 1.0f + gf * gf;
-        p.f32.one_m_g = 1.0f - gf;
-        p.f32.two_g = 2.0f * gf;
-        p.f32.inv_2g = p.hg_iso ? 0.0f : (float)(1.0 / (2.0 * h->g));
-    }
-    p.f32.s_max = (float)p.s_max;
-    p.f32.rr_weight = (float)h->rr_weight;
-    p.f32.rr_mult = (float)h->rr_mult;
-    p.f32.rr_p = (float)(1.0 / h->rr_mult);
-    p.f32.rr_gain = (float)(h->rr_mult - 1.0);
-    p.f32.hist_scale = (float)(256.0 / (4.0 * (double)h->nz));
+    fill_f32(h, p.s_max, p.f32, p.hg_iso, p.small_x);
 
     CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
     CUDA_TRY(f64 ? launch_transport_f64(p, field, blocks, h->threads, smem, s)
@@ -977,4 +982,293 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     out->status = (flags & F_ITER_LIMIT) ? SP_ESTEPLIMIT : SP_OK;
     if (out->status != SP_OK) return fail(out->status, "step limit");
     return SP_OK;
+}
+
+// ------------------------------------------------------------------------
+// Batched launches: many masks of uneven size and optics in one persistent
+// launch (a device table of problems, one shared photon-claim counter), an
+// optional CUDA graph of {counter reset, transport, photon-id advance} that
+// later runs replay, and a host autotuner over threads per CTA, CTAs per SM
+// and the warp compaction threshold.
+// ------------------------------------------------------------------------
+
+// After a batched launch, every problem's next photon ids start past the
+// photons just run (lets a captured graph be replayed as further runs).
+__global__ void batch_advance_kernel(BatchProblem *table, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) table[i].pid_begin += table[i].n_photons;
+}
+
+struct sp_mc_batch {
+    int device = 0, sm_count = 0, n = 0;
+    std::vector<sp_mc *> h;
+    std::vector<BatchProblem> table;
+    BatchProblem *d_table = nullptr;
+    u64 *d_next = nullptr;
+    int threads = 128, blocks_per_sm = 0, compact_k = 8, use_graph = 1;
+    bool table_valid = false;              // device table matches table[]
+    std::vector<u64> cfg_n;                // configuration of the device table / graph
+    u64 cfg_seed = 0;
+    cudaStream_t cap = nullptr;            // private stream for graph capture
+    cudaGraphExec_t exec = nullptr;
+    int graph_threads = 0, graph_blocks = 0, graph_compact = 0;
+};
+
+static void batch_free(sp_mc_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_table);
+    cudaFree(b->d_next);
+    for (sp_mc *x : b->h) {
+        if (x) { free_all(x); delete x; }
+    }
+    b->h.clear();
+}
+
+extern "C" sp_mc_batch_t *sp_mc_batch_create(int n, const uint8_t *const *masks, const int *dims,
+                                             const double *optics) {
+    g_err.clear();
+    if (n < 1 || !masks || !dims || !optics) { fail(SP_EINVAL, "bad batch arguments"); return nullptr; }
+    sp_mc_batch *b = new (std::nothrow) sp_mc_batch();
+    if (!b) { fail(SP_ENOMEM, "host allocation failed"); return nullptr; }
+    b->n = n;
+    for (int i = 0; i < n; ++i) {
+        sp_mc *h = sp_mc_create(masks[i], dims[3 * i], dims[3 * i + 1], dims[3 * i + 2],
+                                optics[4 * i], optics[4 * i + 1], optics[4 * i + 2], optics[4 * i + 3]);
+        if (!h) {
+            const std::string msg = std::string("problem ") + std::to_string(i) + ": " + g_err;
+            batch_free(b);
+            delete b;
+            fail(SP_EINVAL, "%s", msg.c_str());
+            return nullptr;
+        }
+        b->h.push_back(h);
+    }
+    b->device = b->h[0]->device;
+    b->sm_count = b->h[0]->sm_count;
+    b->table.resize(n);
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_table, n * sizeof(BatchProblem))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_next, sizeof(u64))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        fail(SP_ENOMEM, "batch allocation: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    return b;
+}
+
+extern "C" void sp_mc_batch_destroy(sp_mc_batch_t *b) {
+    if (!b) return;
+    DeviceGuard guard(b->device);
+    batch_free(b);
+    delete b;
+}
+
+extern "C" int sp_mc_batch_set_option(sp_mc_batch_t *b, int key, double value) {
+    if (!b) return fail(SP_EINVAL, "null batch");
+    switch (key) {
+    case SP_OPT_THREADS: {
+        const int t = (int)value;
+        if (t < 32 || t > 256 || t % 32) return fail(SP_EINVAL, "threads must be a multiple of 32 in [32, 256]");
+        b->threads = t; return SP_OK;
+    }
+    case SP_OPT_BLOCKS:     // CTAs per SM for batched launches; 0 = as many as fit
+        if (value < 0 || value > 32) return fail(SP_EINVAL, "CTAs per SM must be in [0, 32]");
+        b->blocks_per_sm = (int)value; return SP_OK;
+    case SP_OPT_COMPACT:
+        if (value < 1 || value > 32) return fail(SP_EINVAL, "compaction threshold must be in [1, 32]");
+        b->compact_k = (int)value; return SP_OK;
+    case SP_OPT_GRAPH:
+        b->use_graph = value != 0; return SP_OK;
+    default: {
+        // optics-independent per-problem options apply to every problem
+        if (key == SP_OPT_TALLY_FIELD || key == SP_OPT_PRECISION || key == SP_OPT_RECORDS ||
+            key == SP_OPT_PID_OFFSET)
+            return fail(SP_EINVAL, "option %d is fixed for batched launches", key);
+        for (sp_mc *h : b->h) {
+            const int rc = sp_mc_set_option(h, key, value);
+            if (rc) return rc;
+        }
+        b->table_valid = false;
+        return SP_OK;
+    }
+    }
+}
+
+extern "C" int sp_mc_batch_get_option(const sp_mc_batch_t *b, int key, double *value) {
+    if (!b || !value) return fail(SP_EINVAL, "null argument");
+    switch (key) {
+    case SP_OPT_THREADS: *value = b->threads; return SP_OK;
+    case SP_OPT_BLOCKS: *value = b->blocks_per_sm; return SP_OK;
+    case SP_OPT_COMPACT: *value = b->compact_k; return SP_OK;
+    case SP_OPT_GRAPH: *value = b->use_graph; return SP_OK;
+    default: return sp_mc_get_option(b->h[0], key, value);
+    }
+}
+
+static int batch_launch(sp_mc_batch *b, u64 total, cudaStream_t s) {
+    int per_sm = 0;
+    CUDA_TRY(occupancy_batch(b->threads, &per_sm));
+    if (per_sm < 1) return fail(SP_ECUDA, "batched transport cannot be resident with %d threads", b->threads);
+    if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
+    BatchParams bp{};
+    bp.problems = b->d_table;
+    bp.n_problems = b->n;
+    bp.total_photons = total;
+    bp.next = b->d_next;
+    bp.key0 = (u32)b->cfg_seed;
+    bp.key1 = (u32)(b->cfg_seed >> 32);
+    bp.compact_k = b->compact_k;
+    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, sizeof(u64), s));
+    CUDA_TRY(launch_transport_batch(bp, per_sm * b->sm_count, b->threads, s));
+    batch_advance_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_table, b->n);
+    CUDA_TRY(cudaGetLastError());
+    b->graph_threads = b->threads;
+    b->graph_blocks = per_sm;
+    b->graph_compact = b->compact_k;
+    return SP_OK;
+}
+
+extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed,
+                               void *stream) {
+    if (!b || !n_photons) return fail(SP_EINVAL, "null argument");
+    DeviceGuard guard(b->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    u64 total = 0;
+    for (int i = 0; i < b->n; ++i) total += n_photons[i];
+    if (total == 0) return SP_OK;
+    const std::vector<u64> want(n_photons, n_photons + b->n);
+    const bool same_cfg = b->table_valid && want == b->cfg_n && seed == b->cfg_seed;
+    if (!same_cfg) {
+        // (re)build the device table from the handles' photon counters
+        u64 offset = 0;
+        for (int i = 0; i < b->n; ++i) {
+            sp_mc *h = b->h[i];
+            BatchProblem &t = b->table[i];
+            t = BatchProblem{};
+            t.bricks = h->d_bricks;
+            t.field = h->d_field;
+            t.tal = h->d_tal;
+            t.nx = h->nx; t.ny = h->ny; t.nz = h->nz;
+            t.nbx = h->nbx; t.nby = h->nby; t.nbz = h->nbz;
+            t.pid_begin = h->pid_offset + h->photons_done;
+            t.n_photons = n_photons[i];
+            t.offset = offset;
+            offset += n_photons[i];
+            const u64 lim = iter_limit(h);
+            t.iter_limit = lim > 0xffffffffull ? 0xffffffffu : (u32)lim;
+            fill_f32(h, path_cap(h), t.f32, t.hg_iso, t.small_x);
+            CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
+        }
+        CUDA_TRY(cudaMemcpyAsync(b->d_table, b->table.data(), b->n * sizeof(BatchProblem),
+                                 cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s));     // the host table may change after return
+        b->cfg_n = want;
+        b->cfg_seed = seed;
+        b->table_valid = true;
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    }
+    if (b->use_graph) {
+        int per_sm = 0;
+        CUDA_TRY(occupancy_batch(b->threads, &per_sm));
+        if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
+        if (b->exec && (b->graph_threads != b->threads || b->graph_blocks != per_sm ||
+                        b->graph_compact != b->compact_k)) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        if (!b->exec) {
+            // capture {counter reset, transport, id advance} once; later runs replay it
+            CUDA_TRY(cudaStreamSynchronize(s));
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            const int rc = batch_launch(b, total, b->cap);
+            const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+            if (e != cudaSuccess) return fail(SP_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            const cudaError_t e2 = cudaGraphInstantiate(&b->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e2 != cudaSuccess) { b->exec = nullptr; return fail(SP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2)); }
+        }
+        CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    } else {
+        const int rc = batch_launch(b, total, s);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < b->n; ++i) b->h[i]->photons_done += n_photons[i];
+    return SP_OK;
+}
+
+extern "C" int sp_mc_batch_tallies(sp_mc_batch_t *b, int i, sp_mc_result_t *out, void *stream) {
+    if (!b || i < 0 || i >= b->n) return fail(SP_EINVAL, "problem index out of range");
+    return sp_mc_tallies(b->h[i], out, stream);
+}
+
+extern "C" int sp_mc_batch_raw_field(sp_mc_batch_t *b, int i, uint64_t *dst, int on_device,
+                                     void *stream) {
+    if (!b || i < 0 || i >= b->n) return fail(SP_EINVAL, "problem index out of range");
+    return sp_mc_raw_field(b->h[i], dst, on_device, stream);
+}
+
+extern "C" int sp_mc_batch_reset(sp_mc_batch_t *b, void *stream) {
+    if (!b) return fail(SP_EINVAL, "null batch");
+    for (sp_mc *h : b->h) {
+        const int rc = sp_mc_reset(h, stream);
+        if (rc) return rc;
+    }
+    b->table_valid = false;
+    return SP_OK;
+}
+
+extern "C" int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed,
+                                    double *photons_per_s, void *stream) {
+    if (!b || !n_photons) return fail(SP_EINVAL, "null argument");
+    DeviceGuard guard(b->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int saved_graph = b->use_graph;
+    b->use_graph = 0;
+    u64 total = 0;
+    for (int i = 0; i < b->n; ++i) total += n_photons[i];
+    if (total == 0) return fail(SP_EINVAL, "autotuning needs photons");
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int threads_c[] = {64, 128, 256};
+    const int compact_c[] = {4, 8, 12, 16};
+    double best = -1.0;
+    int best_t = b->threads, best_b = b->blocks_per_sm, best_k = b->compact_k;
+    int rc = SP_OK;
+    for (int t : threads_c) {
+        int per_sm = 0;
+        if (occupancy_batch(t, &per_sm) != cudaSuccess || per_sm < 1) continue;
+        for (int bps : {per_sm, (per_sm + 1) / 2}) {
+            for (int k : compact_c) {
+                b->threads = t;
+                b->blocks_per_sm = bps;
+                b->compact_k = k;
+                cudaEventRecord(e0, s);
+                if ((rc = sp_mc_batch_run(b, n_photons, seed, stream)) != SP_OK) goto done;
+                cudaEventRecord(e1, s);
+                float ms = 0;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    rc = fail(SP_ECUDA, "autotune timing failed");
+                    goto done;
+                }
+                const double rate = (double)total / (ms * 1e-3);
+                if (rate > best) { best = rate; best_t = t; best_b = bps; best_k = k; }
+            }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->threads = best_t;
+    b->blocks_per_sm = best_b;
+    b->compact_k = best_k;
+    b->use_graph = saved_graph;
+    if (rc) return rc;
+    if (photons_per_s) *photons_per_s = best;
+    return sp_mc_batch_reset(b, stream);     // the calibration runs leave no tallies behind
 }

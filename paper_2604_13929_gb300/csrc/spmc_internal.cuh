@@ -68,12 +68,38 @@ struct TransportParams {
     } f32;
 };
 
+// One problem of a batched launch: its own mask bricks, voxel field and
+// tallies, dimensions and FP32 optics.  Photons of all problems share one
+// claim counter: global index k belongs to the problem whose
+// [offset, offset + n_photons) contains it, with photon id pid_begin + k - offset.
+struct BatchProblem {
+    const u64 *bricks;
+    u64 *field;
+    DevTallies *tal;
+    int nx, ny, nz, nbx, nby, nbz;
+    u64 pid_begin, n_photons, offset;
+    u32 iter_limit;
+    int hg_iso, small_x;
+    TransportParams::F32 f32;
+};
+
+struct BatchParams {
+    const BatchProblem *problems;   // device table
+    int n_problems;
+    u64 total_photons;              // sum of n_photons (one run)
+    u64 *next;                      // claim counter, zeroed before each launch
+    u32 key0, key1;                 // Philox key = seed (shared by all problems)
+    int compact_k;
+};
+
 // Launch helpers (defined in the per-precision translation units).
 cudaError_t launch_transport_f32(const TransportParams &p, bool field, int blocks, int threads,
                                  size_t smem, cudaStream_t s);
 cudaError_t launch_transport_f64(const TransportParams &p, bool field, int blocks, int threads,
                                  size_t smem, cudaStream_t s);
 cudaError_t occupancy_f32(bool field, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_transport_batch(const BatchParams &b, int blocks, int threads, cudaStream_t s);
+cudaError_t occupancy_batch(int threads, int *blocks_per_sm);
 cudaError_t occupancy_f64(bool field, int threads, size_t smem, int *blocks_per_sm);
 const void *kernel_f32(bool field);
 const void *kernel_f64(bool field);

@@ -163,8 +163,14 @@ enum { M_STEP = 0, M_EVENT = 1, M_NEW = 2, M_DONE = 3 };
 #define SPMC_MIN_BLOCKS 1
 #endif
 
-template <typename Real, bool kField>
-__global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const TransportParams p) {
+// Batched launches (kBatch): many problems (masks, sizes, optics) in one
+// persistent launch.  A lane loads its problem's dimensions, optics and
+// pointers when it claims a photon, so one warp can carry photons of
+// different problems; per-photon tallies go straight to the problem's global
+// integer tallies.
+template <typename Real, bool kField, bool kBatch>
+__global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const TransportParams p,
+                                                                          const BatchParams bp) {
     using O = Ops<Real>;
     constexpr bool kExact = sizeof(Real) == 8;
     extern __shared__ u64 s_bricks[];
@@ -173,15 +179,21 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
     {   // zero the block tallies, stage the entry slab of the mask
         u64 *z = reinterpret_cast<u64 *>(&st);
         for (int i = threadIdx.x; i < (int)(sizeof(SmemTallies) / 8); i += blockDim.x) z[i] = 0;
-        for (int i = threadIdx.x; i < p.smem_bricks; i += blockDim.x) s_bricks[i] = __ldg(p.bricks + i);
+        if constexpr (!kBatch)
+            for (int i = threadIdx.x; i < p.smem_bricks; i += blockDim.x) s_bricks[i] = __ldg(p.bricks + i);
     }
     __syncthreads();
 
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int nbx = p.nbx, nby = p.nby;
+    int nx = p.nx, ny = p.ny, nz = p.nz;
+    int nbx = p.nbx, nby = p.nby;
+    const u64 *bricks_ptr = p.bricks;            // per lane in batched launches
+    u64 *field_ptr = p.field;
+    DevTallies *tal_ptr = p.tal;
+    const u32 key0 = kBatch ? bp.key0 : p.key0, key1 = kBatch ? bp.key1 : p.key1;
+    int prob = 0;
     Real mus, mua, inv_mus, inv_mua, one_m_g2, one_p_g2, one_m_g, two_g, inv_2g, g;
     Real s_max, rr_w, rr_m, rr_p, rr_gain, hist_scale;
     if constexpr (kExact) {
@@ -202,12 +214,13 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
         s_max = p.f32.s_max; rr_w = p.f32.rr_weight; rr_m = p.f32.rr_mult;
         rr_p = p.f32.rr_p; rr_gain = p.f32.rr_gain; hist_scale = p.f32.hist_scale;
     }
-    const bool absorb_on = mua > 0;
-    const bool small_x = p.small_x != 0;
-    const bool hg_iso = p.hg_iso != 0;
+    bool absorb_on = mua > 0;
+    bool small_x = p.small_x != 0;
+    bool hg_iso = p.hg_iso != 0;
     const Real kInf = O::inf();
-    const u32 iter_limit = p.iter_limit > 0xffffffffull ? 0xffffffffu : (u32)p.iter_limit;
-    const int compact_k = p.compact_k < 1 ? 1 : (p.compact_k > 32 ? 32 : p.compact_k);
+    u32 iter_limit = p.iter_limit > 0xffffffffull ? 0xffffffffu : (u32)p.iter_limit;
+    const int ck = kBatch ? bp.compact_k : p.compact_k;
+    const int compact_k = ck < 1 ? 1 : (ck > 32 ? 32 : ck);
 
     // photon state
     int mode = M_NEW;
@@ -233,7 +246,8 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
         return (u32)(((z & 3) << 4) | ((y & 3) << 2) | (x & 3));
     };
     auto fetch = [&](u32 b) -> u64 {
-        return ((int)b < p.smem_bricks) ? s_bricks[b] : __ldg(p.bricks + b);
+        if constexpr (kBatch) return __ldg(bricks_ptr + b);
+        else return ((int)b < p.smem_bricks) ? s_bricks[b] : __ldg(p.bricks + b);
     };
     (void)nbxy;
     auto q32 = [&](Real c) -> u64 {
@@ -243,29 +257,35 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
 
     auto finish = [&](int kind) {
         // kind: 1 R, 2 T, 3 roulette, 4 path cap
+        u64 (*tb)[B_N] = st.batch;
+        u64 *tc = st.counts, *th = st.hist, *ts = st.sums;
+        if constexpr (kBatch) {
+            tb = tal_ptr->batch; tc = tal_ptr->counts; th = tal_ptr->hist; ts = tal_ptr->sums;
+            hist_scale = bp.problems[prob].f32.hist_scale;
+        }
         if (kind == 1 || kind == 2) {
             const u64 qw = q32(w);
-            atomicAdd(&st.batch[batch][kind == 1 ? B_R : B_T], qw);
+            atomicAdd(&tb[batch][kind == 1 ? B_R : B_T], qw);
             int hb = (int)(P * hist_scale);
             hb = hb > 256 ? 256 : (hb < 0 ? 0 : hb);
-            atomicAdd(&st.hist[hb], qw);
-            atomic_add_u128(&st.sums[0], qw);
-            atomic_add_u128(&st.sums[2], O::q32(w * P));
-            atomic_add_u128(&st.sums[4], O::q16(w * P * P));
-            atomicAdd(&st.counts[kind == 1 ? C_EXIT_R : C_EXIT_T], 1ull);
+            atomicAdd(&th[hb], qw);
+            atomic_add_u128(&ts[0], qw);
+            atomic_add_u128(&ts[2], O::q32(w * P));
+            atomic_add_u128(&ts[4], O::q16(w * P * P));
+            atomicAdd(&tc[kind == 1 ? C_EXIT_R : C_EXIT_T], 1ull);
         } else if (kind == 3) {
-            atomicAdd(&st.batch[batch][B_LOST], q32(w));
-            atomicAdd(&st.counts[C_RR_KILL], 1ull);
+            atomicAdd(&tb[batch][B_LOST], q32(w));
+            atomicAdd(&tc[C_RR_KILL], 1ull);
         } else {
-            atomicAdd(&st.batch[batch][B_GATED], q32(w));
-            atomicAdd(&st.counts[C_GATED], 1ull);
+            atomicAdd(&tb[batch][B_GATED], q32(w));
+            atomicAdd(&tc[C_GATED], 1ull);
         }
-        atomicAdd(&st.batch[batch][B_A], q32(A));
-        atomicAdd(&st.batch[batch][B_PHOTONS], 1ull);
-        atomicAdd(&st.counts[C_INTERACT], (u64)n_int);
-        atomicAdd(&st.counts[C_SCATTER], (u64)n_scat);
-        atomicAdd(&st.counts[C_RR_SURV], (u64)n_surv);
-        atomicAdd(&st.counts[C_STEPS], (u64)n_steps);
+        atomicAdd(&tb[batch][B_A], q32(A));
+        atomicAdd(&tb[batch][B_PHOTONS], 1ull);
+        atomicAdd(&tc[C_INTERACT], (u64)n_int);
+        atomicAdd(&tc[C_SCATTER], (u64)n_scat);
+        atomicAdd(&tc[C_RR_SURV], (u64)n_surv);
+        atomicAdd(&tc[C_STEPS], (u64)n_steps);
         if (pid - p.rec_base < p.n_rec) {
             long long *ri = p.rec_ints + (pid - p.rec_base) * 4;
             double *rv = p.rec_vals + (pid - p.rec_base) * 4;
@@ -333,7 +353,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
             if (!(seg > 0)) seg = 0;
             ev = 2;
         }
-        if (++iters > iter_limit) { ev = 2; atomicOr(&p.tal->flags, (u32)F_ITER_LIMIT); }
+        if (++iters > iter_limit) { ev = 2; atomicOr(&tal_ptr->flags, (u32)F_ITER_LIMIT); }
 
         if (seg > 0) {
             Real dep;
@@ -359,7 +379,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
             }
             const u64 q = q32(dep);
             if constexpr (kField) {
-                if (q) atomicAdd(p.field + (((u64)brick << 6) | bit), q);
+                if (q) atomicAdd(field_ptr + (((u64)brick << 6) | bit), q);
             } else {
                 atomicAdd(&st.depth[pore ? 1 : 0][bin], q);
             }
@@ -415,22 +435,49 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
             if (want) {
                 const int leader = __ffs(want) - 1;
                 u64 base = 0;
-                if (lane == leader) base = atomicAdd(&p.tal->next, (u64)__popc(want));
+                if (lane == leader) base = atomicAdd(kBatch ? bp.next : &p.tal->next, (u64)__popc(want));
                 base = __shfl_sync(kFull, base, leader);
                 if (mode == M_NEW) {
                     const u64 k = base + (u64)__popc(want & lt_mask);
-                    if (k >= p.n_photons) {
+                    if (k >= (kBatch ? bp.total_photons : p.n_photons)) {
                         mode = M_DONE;
                     } else {
-                        pid = p.pid_begin + k;
+                        if constexpr (kBatch) {
+                            // the problem owning global index k (last offset <= k)
+                            int lo = 0, hi = bp.n_problems - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (bp.problems[mid].offset <= k) lo = mid; else hi = mid - 1;
+                            }
+                            prob = lo;
+                            const BatchProblem &pr = bp.problems[prob];
+                            pid = pr.pid_begin + (k - pr.offset);
+                            nx = pr.nx; ny = pr.ny; nz = pr.nz; nbx = pr.nbx; nby = pr.nby;
+                            bricks_ptr = pr.bricks; field_ptr = pr.field; tal_ptr = pr.tal;
+                            mus = pr.f32.mus; mua = pr.f32.mua;
+                            inv_mus = pr.f32.inv_mus; inv_mua = pr.f32.inv_mua;
+                            s_max = pr.f32.s_max;
+                            absorb_on = mua > 0;
+                            small_x = pr.small_x != 0;
+                            iter_limit = pr.iter_limit;
+                        } else {
+                            pid = p.pid_begin + k;
+                        }
                         event = 0;
                         mode = M_EVENT;
                     }
                 }
             }
             if (mode == M_EVENT) {
+                if constexpr (kBatch) {   // event-time optics of this lane's problem
+                    const TransportParams::F32 &f = bp.problems[prob].f32;
+                    one_m_g2 = f.one_m_g2; one_p_g2 = f.one_p_g2; one_m_g = f.one_m_g;
+                    two_g = f.two_g; inv_2g = f.inv_2g;
+                    rr_w = f.rr_weight; rr_m = f.rr_mult; rr_p = f.rr_p; rr_gain = f.rr_gain;
+                    hg_iso = bp.problems[prob].hg_iso != 0;
+                }
                 u32 r[4];
-                philox4x32_10(event, 0u, (u32)pid, (u32)(pid >> 32), p.key0, p.key1, r);
+                philox4x32_10(event, 0u, (u32)pid, (u32)(pid >> 32), key0, key1, r);
                 if (event == 0) {
                     // ---- launch: uniform over the z = 0 face, +z ----------
                     const Real xr = O::uniform(r[0]) * (Real)nx;
@@ -454,7 +501,8 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
                     bit = bit_of(ix, iy, 0);
                     bin = 0;
                     word = fetch(brick);
-                    atomicAdd(&st.counts[C_LAUNCHED], 1ull);
+                    if constexpr (kBatch) atomicAdd(&tal_ptr->counts[C_LAUNCHED], 1ull);
+                    else atomicAdd(&st.counts[C_LAUNCHED], 1ull);
                     mode = M_STEP;
                     if (pid - p.rec_base < p.n_rec) {
                         double *site = p.rec_sites + (pid - p.rec_base) * 24;
@@ -485,7 +533,8 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
                     bool alive = true;
                     if (w < rr_w) {
                         if (O::uniform(r[3]) < rr_p) {
-                            atomicAdd(&st.batch[batch][B_GAIN], q32(w * rr_gain));
+                            if constexpr (kBatch) atomicAdd(&tal_ptr->batch[batch][B_GAIN], q32(w * rr_gain));
+                            else atomicAdd(&st.batch[batch][B_GAIN], q32(w * rr_gain));
                             w = w * rr_m;
                             ++n_surv;
                         } else {
@@ -568,6 +617,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
     }
 
     // ---- retire: flush the block tallies with integer atomics -----------
+    if constexpr (kBatch) return;
     __syncthreads();
     DevTallies *g_t = p.tal;
     for (int i = threadIdx.x; i < kNBatch * B_N; i += blockDim.x) {
@@ -594,21 +644,23 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
 template <typename Real>
 cudaError_t launch_transport(const TransportParams &p, bool field, int blocks, int threads,
                              size_t smem, cudaStream_t s) {
-    if (field) transport_kernel<Real, true><<<blocks, threads, smem, s>>>(p);
-    else transport_kernel<Real, false><<<blocks, threads, smem, s>>>(p);
+    const BatchParams none{};
+    if (field) transport_kernel<Real, true, false><<<blocks, threads, smem, s>>>(p, none);
+    else transport_kernel<Real, false, false><<<blocks, threads, smem, s>>>(p, none);
     return cudaGetLastError();
 }
 
 template <typename Real>
 const void *kernel_ptr(bool field) {
-    return field ? reinterpret_cast<const void *>(&transport_kernel<Real, true>)
-                 : reinterpret_cast<const void *>(&transport_kernel<Real, false>);
+    return field ? reinterpret_cast<const void *>(&transport_kernel<Real, true, false>)
+                 : reinterpret_cast<const void *>(&transport_kernel<Real, false, false>);
 }
 
 template <typename Real>
 cudaError_t occupancy(bool field, int threads, size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, field ? transport_kernel<Real, true> : transport_kernel<Real, false>,
+        blocks_per_sm,
+        field ? transport_kernel<Real, true, false> : transport_kernel<Real, false, false>,
         threads, smem);
 }
 

@@ -14,4 +14,17 @@ cudaError_t occupancy_f32(bool field, int threads, size_t smem, int *blocks_per_
 
 const void *kernel_f32(bool field) { return kernel_ptr<float>(field); }
 
+cudaError_t launch_transport_batch(const BatchParams &b, int blocks, int threads, cudaStream_t s) {
+    TransportParams p{};
+    p.compact_k = b.compact_k;
+    transport_kernel<float, true, true><<<blocks, threads, 0, s>>>(p, b);
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_batch(int threads, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                         transport_kernel<float, true, true>,
+                                                         threads, 0);
+}
+
 }  // namespace spmc

@@ -31,23 +31,30 @@ def initial_noise(shape, seed: int, amplitude: float = 0.05) -> np.ndarray:
 
 
 def cahn_hilliard(shape, steps: int, seed: int = 0, dt: float = 0.1,
-                  device: str | torch.device = "cpu") -> torch.Tensor:
-    """Integrate c_t = lap(c^3 - c - lap c) from seeded noise; returns float64 c."""
+                  device: str | torch.device = "cpu", dtype=torch.float64,
+                  seeds=None) -> torch.Tensor:
+    """Integrate c_t = lap(c^3 - c - lap c) from seeded noise; returns c.
+
+    ``seeds`` (a list) integrates several same-shape fields at once, one per
+    seed, stacked along a leading axis."""
     nz, ny, nx = shape
     dev = torch.device(device)
-    c = torch.from_numpy(initial_noise(shape, seed)).to(dev)
-    kz = 2 * math.pi * torch.fft.fftfreq(nz, d=1.0, dtype=torch.float64, device=dev)
-    ky = 2 * math.pi * torch.fft.fftfreq(ny, d=1.0, dtype=torch.float64, device=dev)
-    kx = 2 * math.pi * torch.fft.rfftfreq(nx, d=1.0, dtype=torch.float64, device=dev)
+    many = seeds is not None
+    noise = np.stack([initial_noise(shape, sd) for sd in (seeds if many else [seed])])
+    c = torch.from_numpy(noise).to(device=dev, dtype=dtype)
+    kz = 2 * math.pi * torch.fft.fftfreq(nz, d=1.0, dtype=dtype, device=dev)
+    ky = 2 * math.pi * torch.fft.fftfreq(ny, d=1.0, dtype=dtype, device=dev)
+    kx = 2 * math.pi * torch.fft.rfftfreq(nx, d=1.0, dtype=dtype, device=dev)
     k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
     num = dt * k2
     den = 1.0 + dt * k2 * k2
-    c_hat = torch.fft.rfftn(c)
+    dims = (-3, -2, -1)
+    c_hat = torch.fft.rfftn(c, dim=dims)
     for _ in range(int(steps)):
-        nl = torch.fft.rfftn(c * c * c - c)
+        nl = torch.fft.rfftn(c * c * c - c, dim=dims)
         c_hat = (c_hat - num * nl) / den
-        c = torch.fft.irfftn(c_hat, s=(nz, ny, nx))
-    return c
+        c = torch.fft.irfftn(c_hat, s=(nz, ny, nx), dim=dims)
+    return c if many else c[0]
 
 
 def rank_threshold(c, porosity: float) -> np.ndarray:
@@ -67,6 +74,33 @@ def spinodal_mask(n: int | tuple, porosity: float, steps: int, seed: int = 0,
     """Cahn-Hilliard spinodal mask of shape n^3 (or (nz, ny, nx))."""
     shape = (n, n, n) if isinstance(n, int) else tuple(n)
     return rank_threshold(cahn_hilliard(shape, steps, seed=seed, device=device), porosity)
+
+
+def batch_workload(n_masks: int = 64, seed: int = 3, ch_steps: int = 1000,
+                   sizes=(64, 96, 128, 160, 192, 224, 256), device: str | None = None):
+    """Masks of uneven size and random optics for batched launches.
+
+    Sizes are drawn from ``sizes`` (cubes), porosity from U[0.50, 0.95], solid
+    mu_s h log-uniform on [0.1, 2.0], mu_a h uniform on [0.001, 0.05], g
+    uniform on [0, 0.9] (numpy default_rng(seed)).  Each mask is a
+    Cahn-Hilliard field of ``ch_steps`` steps in FP32 from noise seed
+    1000 + i, rank-thresholded to its porosity.  Returns a list of
+    (mask, mu_s h, mu_a h, g)."""
+    rng = np.random.default_rng(seed)
+    size = rng.choice(np.asarray(sizes), n_masks)
+    phi = rng.uniform(0.50, 0.95, n_masks)
+    mus = np.exp(rng.uniform(np.log(0.1), np.log(2.0), n_masks))
+    mua = rng.uniform(0.001, 0.05, n_masks)
+    g = rng.uniform(0.0, 0.9, n_masks)
+    dev = device or default_device()
+    masks = [None] * n_masks
+    for n in np.unique(size):
+        idx = [i for i in range(n_masks) if size[i] == n]
+        c = cahn_hilliard((int(n),) * 3, ch_steps, device=dev, dtype=torch.float32,
+                          seeds=[1000 + i for i in idx])
+        for j, i in enumerate(idx):
+            masks[i] = rank_threshold(c[j], float(phi[i]))
+    return [(masks[i], float(mus[i]), float(mua[i]), float(g[i])) for i in range(n_masks)]
 
 
 def default_device() -> str:

@@ -28,7 +28,7 @@ SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_ESTEPLIMIT, SP_EOVERFLOW = 0, -1, -2, 
 NBATCH, NBIN, NHIST = 16, 64, 257
 OPT = {"path_cap": 1, "rr_weight": 2, "rr_mult": 3, "tally_field": 4, "precision": 5,
        "records": 6, "blocks": 7, "threads": 8, "iter_limit": 9, "smem_bricks": 10,
-       "pid_offset": 11, "compact": 12}
+       "pid_offset": 11, "compact": 12, "graph": 13}
 ERR_NAMES = {SP_EINVAL: "SP_EINVAL", SP_ENOMEM: "SP_ENOMEM", SP_ECUDA: "SP_ECUDA",
              SP_ESTEPLIMIT: "SP_ESTEPLIMIT", SP_EOVERFLOW: "SP_EOVERFLOW"}
 
@@ -116,6 +116,15 @@ def load() -> ctypes.CDLL:
             "sp_mc_last_error": (ctypes.c_char_p, []),
             "sp_mc_version": (ctypes.c_char_p, []),
             "sp_mc_result_size": (sz, []),
+            "sp_mc_batch_create": (vp, [ctypes.c_int, vp, vp, vp]),
+            "sp_mc_batch_set_option": (ctypes.c_int, [vp, ctypes.c_int, _D]),
+            "sp_mc_batch_get_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(_D)]),
+            "sp_mc_batch_run": (ctypes.c_int, [vp, vp, _U64, vp]),
+            "sp_mc_batch_tallies": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Result), vp]),
+            "sp_mc_batch_raw_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp]),
+            "sp_mc_batch_reset": (ctypes.c_int, [vp, vp]),
+            "sp_mc_batch_autotune": (ctypes.c_int, [vp, vp, _U64, ctypes.POINTER(_D), vp]),
+            "sp_mc_batch_destroy": (None, [vp]),
             "sp_mc_probe_step_ceiling": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_longlong,
                                                         ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -285,6 +294,86 @@ def sp_mc_simulate_noalloc(d_mask, nx: int, ny: int, nz: int, voxel_h: float, mu
 
 
 # ------------------------------------------------------------ convenience --
+
+class Batch:
+    """Many masks (uneven sizes, per-problem optics) in one persistent launch.
+
+    ``problems`` is a list of (mask, mu_s, mu_a, g) or (mask, mu_s, mu_a, g,
+    voxel_h); masks are uint8 (nz, ny, nx), 1 = pore.
+    """
+
+    def __init__(self, problems, **options):
+        self.masks = [np.ascontiguousarray(pr[0], dtype=np.uint8) for pr in problems]
+        self.n = len(self.masks)
+        ptrs = (ctypes.c_void_p * self.n)(*[m.ctypes.data for m in self.masks])
+        dims = np.array([[m.shape[2], m.shape[1], m.shape[0]] for m in self.masks],
+                        dtype=np.int32)
+        optics = np.array([[pr[4] if len(pr) > 4 else 1.0, pr[1], pr[2], pr[3]]
+                           for pr in problems], dtype=np.float64)
+        self.handle = load().sp_mc_batch_create(self.n, ptrs, dims.ctypes.data,
+                                                optics.ctypes.data)
+        if not self.handle:
+            raise SpmcError(SP_EINVAL, load().sp_mc_last_error().decode())
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def set_option(self, key, value):
+        _check(load().sp_mc_batch_set_option(self.handle, OPT.get(key, key), float(value)))
+
+    def get_option(self, key) -> float:
+        v = _D()
+        _check(load().sp_mc_batch_get_option(self.handle, OPT.get(key, key), ctypes.byref(v)))
+        return v.value
+
+    def _counts(self, n_photons):
+        n = np.broadcast_to(np.asarray(n_photons, dtype=np.uint64), (self.n,))
+        return np.ascontiguousarray(n)
+
+    def run(self, n_photons, seed: int, stream=None):
+        n = self._counts(n_photons)
+        _check(load().sp_mc_batch_run(self.handle, n.ctypes.data, int(seed) & (2 ** 64 - 1),
+                                      stream_handle(stream)))
+        return self
+
+    def tallies(self, i: int, stream=None) -> dict:
+        r = Result()
+        _check(load().sp_mc_batch_tallies(self.handle, int(i), ctypes.byref(r),
+                                          stream_handle(stream)))
+        return r.to_dict()
+
+    def raw_field(self, i: int, stream=None):
+        out = np.empty(self.masks[i].shape, dtype=np.uint64)
+        _check(load().sp_mc_batch_raw_field(self.handle, int(i), out.ctypes.data, 0,
+                                            stream_handle(stream)))
+        return out
+
+    def reset(self, stream=None):
+        _check(load().sp_mc_batch_reset(self.handle, stream_handle(stream)))
+
+    def autotune(self, n_photons, seed: int, stream=None) -> float:
+        n = self._counts(n_photons)
+        rate = _D()
+        _check(load().sp_mc_batch_autotune(self.handle, n.ctypes.data, int(seed) & (2 ** 64 - 1),
+                                           ctypes.byref(rate), stream_handle(stream)))
+        return rate.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sp_mc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Simulation:
     """Owner of one sp_mc handle.

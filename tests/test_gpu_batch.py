@@ -1,0 +1,88 @@
+"""Batched launches: every problem of a batch equals a separate run.
+
+Each problem's photons use the same ids and key as a separate sp_mc_run on
+its own handle, and the batched kernel performs the same FP32 arithmetic, so
+the integer tallies and the voxel field must agree bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2604_13929_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RAW = ("raw_R", "raw_T", "raw_A", "raw_gated", "raw_lost", "raw_gain", "raw_hist", "raw_depth",
+       "raw_sum_w", "raw_sum_wP", "raw_sum_wP2", "batch_photons")
+COUNTS = ("launched", "interactions", "scatters", "rr_survive", "rr_kill", "exit_R", "exit_T",
+          "gated_n", "steps")
+
+
+@pytest.fixture(scope="module")
+def spmc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_13929_gb300 import build
+    build.build()
+    from paper_2604_13929_gb300 import spmc as s
+    return s
+
+
+@pytest.fixture(scope="module")
+def problems():
+    return [
+        (inputs.spinodal_mask(32, 0.70, 200, seed=1, device="cuda"), 0.5, 0.005, 0.7),
+        (inputs.spinodal_mask((20, 28, 36), 0.85, 200, seed=2, device="cuda"), 1.2, 0.03, 0.3),
+        (inputs.random_mask((13, 9, 22), 0.6, 3), 0.3, 0.01, 0.0),
+        (inputs.spinodal_mask(48, 0.55, 200, seed=4, device="cuda"), 2.0, 0.05, 0.9),
+    ]
+
+
+def _single(spmc, pr, n, seed):
+    sim = spmc.Simulation(pr[0], pr[1], pr[2], pr[3])
+    if n:
+        sim.run(n, seed)
+    t = sim.tallies(check=False)
+    f = sim.raw_field()
+    sim.close()
+    return t, f
+
+
+def _assert_same(a, af, b, bf):
+    for k in RAW:
+        assert np.array_equal(a[k], b[k]), k
+    for k in COUNTS:
+        assert a[k] == b[k], k
+    assert np.array_equal(af, bf)
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_batch_equals_separate_runs(spmc, problems, graph):
+    n = [20000, 15000, 0, 25000]
+    with spmc.Batch(problems, graph=graph) as b:
+        b.run(n, 77)
+        for i, pr in enumerate(problems):
+            ref, rf = _single(spmc, pr, n[i], 77)
+            _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
+
+
+def test_graph_replays_continue_photon_ids(spmc, problems):
+    n = [8000, 6000, 4000, 9000]
+    with spmc.Batch(problems, graph=1) as b:
+        for _ in range(3):
+            b.run(n, 5)
+        for i, pr in enumerate(problems):
+            ref, rf = _single(spmc, pr, 3 * n[i], 5)
+            _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
+
+
+def test_autotune_picks_a_shape_and_leaves_no_tallies(spmc, problems):
+    with spmc.Batch(problems) as b:
+        rate = b.autotune([4000] * 4, 9)
+        assert rate > 0
+        assert b.get_option("threads") in (64, 128, 256)
+        assert 1 <= b.get_option("compact") <= 32
+        assert all(b.tallies(i)["photons"] == 0 for i in range(4))
+        b.run([5000] * 4, 11)
+        for i, pr in enumerate(problems):
+            ref, rf = _single(spmc, pr, 5000, 11)
+            _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
