@@ -44,7 +44,8 @@ class _Problem(ctypes.Structure):
                 ("mask", ctypes.POINTER(ctypes.c_uint8)),
                 ("mus", ctypes.c_double), ("mua", ctypes.c_double), ("g", ctypes.c_double),
                 ("s_max", ctypes.c_double), ("rr_weight", ctypes.c_double),
-                ("rr_mult", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("rr_mult", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("lateral_bc", ctypes.c_int)]
 
 
 _U64 = ctypes.c_uint64
@@ -133,11 +134,13 @@ def default_path_cap(nz: int, porosity: float, mus: float, mua: float, g: float)
 
 def run(mask: np.ndarray, mus: float, mua: float, g: float, n_photons: int, seed: int,
         s_max: float | None = None, pid_begin: int = 0, rr_weight: float = 1e-4,
-        rr_mult: float = 10.0, n_threads: int = 0, field: bool = True, n_rec: int = 0) -> dict:
+        rr_mult: float = 10.0, n_threads: int = 0, field: bool = True, n_rec: int = 0,
+        lateral_bc: str = "periodic") -> dict:
     """Run photons [pid_begin, pid_begin + n_photons) through a mask.
 
     ``mask`` is uint8 (nz, ny, nx), 1 = pore.  ``mus``/``mua`` are the solid
-    coefficients times the voxel edge.  Returns raw integer tallies.
+    coefficients times the voxel edge.  ``lateral_bc`` is "periodic" or
+    "mirror".  Returns raw integer tallies.
     """
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     nz, ny, nx = mask.shape
@@ -145,7 +148,8 @@ def run(mask: np.ndarray, mus: float, mua: float, g: float, n_photons: int, seed
         s_max = default_path_cap(nz, float(mask.mean()), mus, mua, g)
     pb = _Problem(nx, ny, nz, mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                   float(mus), float(mua), float(g), float(s_max), float(rr_weight),
-                  float(rr_mult), int(seed) & 0xFFFFFFFFFFFFFFFF)
+                  float(rr_mult), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                  {"periodic": 0, "mirror": 1}[lateral_bc])
     t = _Tallies()
     fld = np.zeros(mask.shape, dtype=np.uint64) if field else None
     sites = np.zeros((n_rec, 8, 3)) if n_rec else None

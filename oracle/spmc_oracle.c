@@ -13,8 +13,9 @@
  *   Sec. 2.5 media     pore voxels void (mu_a = mu_s = 0), solid voxels scatter
  *                      and absorb;
  *   Sec. 3.5(c)        per-photon cumulative pore path of escaping photons.
- * The lateral faces are periodic and the phase function is Henyey-Greenstein,
- * as the task configuration fixes; n = 1 everywhere (no Fresnel terms).
+ * The lateral faces are periodic (the benchmark configuration) or specular
+ * mirrors (the paper's bc = "mmamma"); the phase function is Henyey-Greenstein;
+ * n = 1 everywhere (no Fresnel terms).
  *
  * The method is a stochastic algorithm, so this file restates its steps in
  * their natural order with the obvious data structures: unwrapped FP64
@@ -275,6 +276,16 @@ static void run_photon(const or_problem_t *pb, uint64_t pid, or_tallies_t *t,
 
         /* cross the face on axis ax */
         p[ax] = (u[ax] > 0.0) ? (double)(iv[ax] + 1) : (double)iv[ax];
+        if (ax < 2 && pb->lateral_bc == 1) {
+            /* mirror lateral faces (Sec. 2.5, bc = "mmamma"): at the domain
+             * edge the direction component is reversed and the photon stays
+             * in its voxel */
+            const long ni = iv[ax] + ((u[ax] > 0.0) ? 1 : -1);
+            if (ni < 0 || ni >= (ax == 0 ? nx : ny)) {
+                u[ax] = -u[ax];
+                continue;
+            }
+        }
         iv[ax] += (u[ax] > 0.0) ? 1 : -1;
         if (ax == 2 && (iv[2] < 0 || iv[2] >= nz)) {
             kind = (iv[2] < 0) ? OR_EXIT_R : OR_EXIT_T;
@@ -338,6 +349,7 @@ int or_run(const or_problem_t *pb, uint64_t pid_begin, uint64_t pid_end,
     if (!pb || !t || !pb->mask || pb->nx < 1 || pb->ny < 1 || pb->nz < 1) return -1;
     if (!(pb->mus >= 0.0) || !(pb->mua >= 0.0) || !(fabs(pb->g) < 1.0)) return -1;
     if (!(pb->s_max > 0.0) || !isfinite(pb->s_max) || !(pb->rr_mult >= 1.0)) return -1;
+    if (pb->lateral_bc != 0 && pb->lateral_bc != 1) return -1;
     if (pid_end < pid_begin) return -1;
 
     int nt = 1;

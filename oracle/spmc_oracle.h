@@ -44,6 +44,7 @@ typedef struct {
     double rr_weight;       /* Russian roulette threshold on w               */
     double rr_mult;         /* survivors are multiplied by this (1/p_survive) */
     uint64_t seed;          /* Philox key = (seed lo, seed hi)               */
+    int lateral_bc;         /* 0 periodic x/y; 1 specular mirrors on x/y     */
 } or_problem_t;
 
 typedef struct {

@@ -369,3 +369,51 @@ def test_printed_estimator_vectors():
         assert abs(e["ratio"] / ratio_m - 1) < 2e-3
         # the prediction evaluated at the printed r
         assert abs(orc.phase_estimators(1.0, r, phi)["predicted_ratio"] - ratio_p) < 3e-4
+
+
+# ------------------------------------------------------ mirror lateral BC --
+
+def _wall_mask():
+    """Pore in x < nx/2, solid beyond, with a solid pocket: the lateral
+    boundary decides whether pore meets pore (mirror) or solid (periodic)."""
+    m = np.zeros((14, 6, 8), dtype=np.uint8)
+    m[:, :, :4] = 1
+    m[5:9, :3, 1] = 0
+    return m
+
+
+def test_mirror_domain_equals_doubled_periodic_domain():
+    """Specular mirrors on x and y are the periodic problem on the domain
+    mirrored to twice the width in x and y: the fluence per unit incident flux
+    across x, folded back onto the original domain, agrees within the
+    seed-to-seed noise, while plain periodic faces differ by several times it."""
+    m = _wall_mask()
+    nz, ny, nx = m.shape
+    dbl = np.concatenate([m, m[:, :, ::-1]], axis=2)
+    dbl = np.concatenate([dbl, dbl[:, ::-1, :]], axis=1)
+    kw = dict(mus=0.8, mua=0.1, g=0.6, n_photons=400000, s_max=1e9)
+
+    def xprof(mask, seed, bc="periodic"):
+        return orc.normalise(orc.run(mask, seed=seed, lateral_bc=bc, **kw))["fluence"]
+
+    fm, fm2, fd, fp = xprof(m, 3, "mirror"), xprof(m, 6, "mirror"), xprof(dbl, 4), xprof(m, 5)
+    fold = (fd[:, :ny, :nx] + fd[:, :ny, 2 * nx - 1:nx - 1:-1] + fd[:, 2 * ny - 1:ny - 1:-1, :nx]
+            + fd[:, 2 * ny - 1:ny - 1:-1, 2 * nx - 1:nx - 1:-1]) / 4
+    pm, pm2, pd, pp = [a.mean(axis=(0, 1)) for a in (fm, fm2, fold, fp)]
+    noise = np.abs(pm - pm2).max()
+    assert np.abs(pm - pd).max() < 1.5 * noise
+    assert np.abs(pm - pp).max() > 3 * noise
+
+
+def test_mirror_keeps_photons_inside_and_uniform_slab_is_unchanged():
+    m = _wall_mask()
+    res = orc.run(m, 0.8, 0.05, 0.6, 3000, 7, n_rec=3000, lateral_bc="mirror")
+    s = res["rec_sites"]
+    ok = np.isfinite(s[..., 0])
+    assert np.all((s[..., 0][ok] >= 0) & (s[..., 0][ok] <= 8))
+    assert np.all((s[..., 1][ok] >= 0) & (s[..., 1][ok] <= 6))
+    kw = dict(mus=0.5, mua=0.02, g=0.7, n_photons=200000)
+    a = orc.normalise(orc.run(inputs.all_solid(10, 3, 3), seed=1, lateral_bc="mirror", **kw))
+    b = orc.normalise(orc.run(inputs.all_solid(10, 3, 3), seed=1, **kw))
+    for k in ("R", "T", "A"):
+        assert abs(a[k] - b[k]) < 4 * math.hypot(a[k + "_se"], b[k + "_se"]) + 1e-6, k
