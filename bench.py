@@ -223,6 +223,51 @@ def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
         print(json.dumps(line), flush=True)
 
 
+def paper_comparison(torch, spmc):
+    """MC at the paper's shell optics (Table tab:optics: g = 0, mu_s' = 20118,
+    mu_a = 5159 m^-1, a_vox = 1.45 um), mirror lateral faces, n = 1, against
+    the collimated diffusion approximation with EMA optics: fluence-weighted
+    RMS_w (Eq. RMSw) for a homogeneous solid slab, the matched EMA slabs and
+    256^3 spinodal masks at porosity 0.70 and 0.90 (Sec. 4.3, Table S1)."""
+    from paper_2604_13929_gb300 import diffusion, inputs
+    h, mus, mua, nz = 1.45e-6, 20118.0, 5159.0, 256
+    L = nz * h
+    out = {"optics": "g=0, mu_s'=20118/m, mu_a=5159/m, a_vox=1.45um, mirror x/y, n=1",
+           "photons": 20_000_000, "cases": {}}
+
+    def run(mask, mus_, mua_):
+        sim = spmc.Simulation(mask, mus_, mua_, 0.0, voxel_h=h, lateral_bc=1)
+        sim.run(out["photons"], SEED)
+        t = sim.tallies()
+        sim.close()
+        return t
+
+    def depth_profile(t, mask):
+        # per-layer mean fluence from the exact per-bin sums (64 bins of 4 layers)
+        return t["depth"][2]
+
+    edges = np.arange(0, 65) * (nz // 64) * h
+    slab = np.zeros((nz, 8, 8), np.uint8)
+    cases = [("homogeneous solid", slab, mus, mua, 0.0)]
+    for phi in (0.70, 0.90):
+        cases.append((f"EMA slab phi={phi}", slab, diffusion.ema(mus, phi), diffusion.ema(mua, phi), phi))
+        cases.append((f"spinodal 256^3 phi={phi}",
+                      inputs.spinodal_mask(256, phi, 4000, seed=0, device="cuda"), mus, mua, phi))
+    for name, mask, ms, ma, phi in cases:
+        t = run(mask, ms, ma)
+        da = diffusion.CollimatedDA(diffusion.ema(mua, phi), diffusion.ema(mus, phi), L, 1.0)
+        prof_da = da.layer_means(edges)
+        prof_mc = depth_profile(t, mask)
+        out["cases"][name] = {
+            "R": t["R"], "T": t["T"], "A": t["A"], "closure": t["closure"],
+            "RMS_w": diffusion.rms_weighted(prof_mc, prof_da),
+            "RMS_unweighted": diffusion.rms_unweighted(prof_mc, prof_da),
+            "RMS_log": diffusion.rms_log(prof_mc, prof_da),
+            "phi_3d": t["phi_3d"], "phi_1d": t["phi_1d"], "ratio": t["ratio"], "r": t["r"],
+            "L_opt_MC1D_um": t["phi_1d"] * L * 1e6, "L_opt_DA_um": da.optical_length * 1e6}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,7 +278,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batch"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch", "paper"],
                     help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
                          "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
     ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
@@ -264,6 +309,10 @@ def main():
 
     if args.workload == "batch":
         batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier)
+        return
+    if args.workload == "paper":
+        if rank == 0:
+            paper_comparison(torch, spmc)
         return
     mask = make_mask("cuda")
     stream = torch.cuda.current_stream()

@@ -75,9 +75,12 @@ enum sp_option {
     SP_OPT_COMPACT     = 12, /* warp compaction threshold in [1, 32]: lanes
                                 needing an interaction or a new photon wait
                                 until this many of their warp do (8)      */
-    SP_OPT_GRAPH       = 13  /* batched launches only: 1 (default) captures
+    SP_OPT_GRAPH       = 13, /* batched launches only: 1 (default) captures
                                 the launch in a CUDA graph and replays it
                                 while photon counts and seed are unchanged */
+    SP_OPT_LATERAL_BC  = 14  /* 0 (default): periodic x and y; 1: specular
+                                mirrors on the lateral faces (the paper's
+                                bc = "mmamma", Sec. 2.5)                  */
 };
 
 typedef struct sp_mc sp_mc_t;   /* opaque, owned by the library */

@@ -73,6 +73,7 @@ struct sp_mc {
     int field = 1, precision = 32, blocks_opt = 0, threads = 256, smem_bricks_opt = 0;
     u64 n_rec = 0, iter_limit_opt = 0, pid_offset = 0;
     int compact_k = 8;
+    int mirror = 0;         // lateral faces: 0 periodic, 1 mirrors
     // device memory
     u64 *d_bricks = nullptr, *d_field = nullptr, *d_layer = nullptr, *d_bin_count = nullptr;
     DevTallies *d_tal = nullptr;
@@ -566,6 +567,9 @@ int sp_mc_set_option(sp_mc_t *h, int key, double value) {
     case SP_OPT_COMPACT:
         if (value < 1 || value > 32) return fail(SP_EINVAL, "compaction threshold must be in [1, 32]");
         h->compact_k = (int)value; return SP_OK;
+    case SP_OPT_LATERAL_BC:
+        if (value != 0 && value != 1) return fail(SP_EINVAL, "lateral BC must be 0 (periodic) or 1 (mirror)");
+        h->mirror = (int)value; return SP_OK;
     case SP_OPT_PID_OFFSET:
         if (value < 0 || value > 1.8e19) return fail(SP_EINVAL, "photon id offset out of range");
         if (h->photons_done) return fail(SP_EINVAL, "the photon id offset can only be set before the first run");
@@ -590,6 +594,7 @@ int sp_mc_get_option(const sp_mc_t *h, int key, double *value) {
     case SP_OPT_SMEM_BRICKS: *value = h->smem_bricks_opt; return SP_OK;
     case SP_OPT_PID_OFFSET: *value = (double)h->pid_offset; return SP_OK;
     case SP_OPT_COMPACT: *value = h->compact_k; return SP_OK;
+    case SP_OPT_LATERAL_BC: *value = h->mirror; return SP_OK;
     default: return fail(SP_EINVAL, "unknown option %d", key);
     }
 }
@@ -645,6 +650,7 @@ int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
     p.rr_mult = h->rr_mult;
     p.iter_limit = iter_limit(h);
     p.compact_k = h->compact_k;
+    p.mirror = h->mirror;
     fill_f32(h, p.s_max, p.f32, p.hg_iso, p.small_x);
 
     CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
@@ -1160,6 +1166,7 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
             const u64 lim = iter_limit(h);
             t.iter_limit = lim > 0xffffffffull ? 0xffffffffu : (u32)lim;
             fill_f32(h, path_cap(h), t.f32, t.hg_iso, t.small_x);
+            t.mirror = h->mirror;
             CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
         }
         CUDA_TRY(cudaMemcpyAsync(b->d_table, b->table.data(), b->n * sizeof(BatchProblem),

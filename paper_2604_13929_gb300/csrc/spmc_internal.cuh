@@ -58,6 +58,7 @@ struct TransportParams {
     u64 iter_limit;
     int compact_k;                 // parked lanes per warp that trigger the event phase
     int hg_iso;                    // |g| < 1e-6: isotropic scattering
+    int mirror;                    // lateral faces: 0 periodic, 1 specular mirrors
     int small_x;                   // mu_a * sqrt(3) <= 0.1: Taylor branch for 1 - exp(-x)
     // The optics again as FP32, converted on the host: in FP32 kernels every
     // constant is a float, so no double-to-float conversion (an FP64-pipe
@@ -79,7 +80,7 @@ struct BatchProblem {
     int nx, ny, nz, nbx, nby, nbz;
     u64 pid_begin, n_photons, offset;
     u32 iter_limit;
-    int hg_iso, small_x;
+    int hg_iso, small_x, mirror;
     TransportParams::F32 f32;
 };
 

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
     DevTallies *tal_ptr = p.tal;
     const u32 key0 = kBatch ? bp.key0 : p.key0, key1 = kBatch ? bp.key1 : p.key1;
     int prob = 0;
+    bool mirror = p.mirror != 0;                 // per lane in batched launches
     Real mus, mua, inv_mus, inv_mua, one_m_g2, one_p_g2, one_m_g, two_g, inv_2g, g;
     Real s_max, rr_w, rr_m, rr_p, rr_gain, hist_scale;
     if constexpr (kExact) {
@@ -332,8 +333,11 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
         int niy = iy + (ax == 1 ? sy : 0);
         const int niz = iz + (ax == 2 ? sz : 0);
         const int wx = (nix >= nx) - (nix < 0), wy = (niy >= ny) - (niy < 0);
-        nix = wx > 0 ? 0 : (wx < 0 ? nx - 1 : nix);
-        niy = wy > 0 ? 0 : (wy < 0 ? ny - 1 : niy);
+        // mirror lateral faces: at the domain edge the photon stays in its
+        // voxel and the crossing component of its direction reverses
+        const bool rx = mirror && wx != 0, ry = mirror && wy != 0;
+        nix = rx ? ix : (wx > 0 ? 0 : (wx < 0 ? nx - 1 : nix));
+        niy = ry ? iy : (wy > 0 ? 0 : (wy < 0 ? ny - 1 : niy));
         const bool leaves = niz < 0 || niz >= nz;
         const u32 nbrick = leaves ? brick : brick_of(nix, niy, niz);
         const u64 nword = (nbrick != brick) ? fetch(nbrick) : word;
@@ -416,7 +420,9 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
             }
         }
         if (leaves) { finish(niz < 0 ? 1 : 2); return; }
-        ix = nix; iy = niy; iz = niz; kx += wx; ky += wy;
+        ix = nix; iy = niy; iz = niz;
+        if (rx) { ux = -ux; sx = -sx; } else kx += wx;
+        if (ry) { uy = -uy; sy = -sy; } else ky += wy;
         brick = nbrick;
         word = nword;
         bit = bit_of(ix, iy, iz);
@@ -460,6 +466,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
                             absorb_on = mua > 0;
                             small_x = pr.small_x != 0;
                             iter_limit = pr.iter_limit;
+                            mirror = pr.mirror != 0;
                         } else {
                             pid = p.pid_begin + k;
                         }

@@ -75,6 +75,16 @@ def test_graph_replays_continue_photon_ids(spmc, problems):
             _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
 
 
+def test_batch_with_mirror_faces_equals_separate_runs(spmc, problems):
+    with spmc.Batch(problems[:2], lateral_bc=1) as b:
+        b.run([12000, 9000], 21)
+        for i, pr in enumerate(problems[:2]):
+            sim = spmc.Simulation(pr[0], pr[1], pr[2], pr[3], lateral_bc=1)
+            sim.run([12000, 9000][i], 21)
+            _assert_same(b.tallies(i), b.raw_field(i), sim.tallies(), sim.raw_field())
+            sim.close()
+
+
 def test_autotune_picks_a_shape_and_leaves_no_tallies(spmc, problems):
     with spmc.Batch(problems) as b:
         rate = b.autotune([4000] * 4, 9)

@@ -413,3 +413,32 @@ def test_max_size_512_cubed_runs(spmc):
     assert abs(t["closure"] - 1) < 1e-6 and abs(t["identity_residual"]) < 1e-12
     assert t["T"] > 0 and t["depth_count"].sum() == 512 ** 3
     sim.close()
+
+
+# ------------------------------------------------------ mirror lateral BC --
+
+def test_mirror_bc_fp64_matches_oracle_per_photon(spmc):
+    """Specular mirrors on x and y (bc = "mmamma"): the FP64 transport
+    reproduces the oracle photon by photon (exactly on a homogeneous slab,
+    >= 99.9 % on a mask with interfaces)."""
+    wall = np.zeros((14, 6, 8), dtype=np.uint8)
+    wall[:, :, :4] = 1
+    wall[5:9, :3, 1] = 0
+    for mask, frac in ((inputs.all_solid(10, 3, 5), 1.0), (wall, 0.999)):
+        n = 20000
+        sim = spmc.Simulation(mask, 0.8, 0.05, 0.6, precision=64, records=n, lateral_bc=1)
+        sim.run(n, 31)
+        _, gi, _ = sim.records(n)
+        sim.close()
+        o = orc.run(mask, 0.8, 0.05, 0.6, n, 31, n_rec=n, lateral_bc="mirror")
+        same = np.all(gi == o["rec_ints"], axis=1)
+        assert same.mean() >= frac, (~same).sum()
+
+
+def test_mirror_bc_fp32_statistics(spmc, c1_mask):
+    sim = spmc.Simulation(c1_mask, MUS, MUA, G, lateral_bc=1)
+    g, gse = _gpu_chunked(sim, c1_mask, 400000, 12)
+    sim.close()
+    o = orc.normalise(orc.run(c1_mask, MUS, MUA, G, 200000, 12, lateral_bc="mirror"))
+    _assert_rta(g, o)
+    _assert_depth(g["depth"][:2], gse, o["depth"], o["depth_se"])
