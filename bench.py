@@ -268,6 +268,86 @@ def paper_comparison(torch, spmc):
     print(json.dumps(out), flush=True)
 
 
+def precision_study(torch, spmc, args):
+    """512^3 porosity-0.90 mask (Cahn-Hilliard, 4000 FP32 steps, seed 0): FP32
+    transport at 1e9 photons; FP32 and FP64 transport on the same 1e6- and
+    1e7-photon subsets; the FP64 CPU oracle on the 1e6 subset.  Per-result
+    errors on identical photon streams, beside the 1e9-photon standard errors."""
+    from oracle import oracle as orc
+    from paper_2604_13929_gb300 import inputs
+    t0 = time.perf_counter()
+    c = inputs.cahn_hilliard((512,) * 3, 4000, seed=0, device="cuda", dtype=torch.float32)
+    mask = inputs.rank_threshold(c, 0.90)
+    del c
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    keys = ("R", "T", "A", "phi_3d", "phi_1d", "phi_pore", "r", "ratio", "pore_path_mean",
+            "escape_weight")
+
+    def gpu(n, precision):
+        sim = spmc.Simulation(mask, MUS, MUA, G, precision=precision)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.run(n, SEED)
+        e1.record()
+        torch.cuda.synchronize()
+        t = sim.tallies()
+        t["_ms"] = e0.elapsed_time(e1)
+        sim.close()
+        return t
+
+    n_sub, n_mid, n_big = 1_000_000, 10_000_000, args.precision_photons
+    f32_sub, f64_sub = gpu(n_sub, 32), gpu(n_sub, 64)
+    f32_mid, f64_mid = gpu(n_mid, 32), gpu(n_mid, 64)
+    f32_big = gpu(n_big, 32)
+    t0 = time.perf_counter()
+    o = orc.normalise(orc.run(mask, MUS, MUA, G, n_sub, SEED, n_threads=os.cpu_count() or 1,
+                              field=False))
+    oracle_s = time.perf_counter() - t0
+
+    def rel(a, b):
+        return float(abs(a - b) / abs(b)) if b else float(abs(a - b))
+
+    def prof_dev(a, b):
+        da, db = np.asarray(a["depth"][:2]), np.asarray(b["depth"][:2])
+        ok = np.isfinite(da) & np.isfinite(db) & (db > 0)
+        return float(np.max(np.abs(da[ok] / db[ok] - 1)))
+
+    table = {}
+    for k in keys:
+        table[k] = {"oracle_1e6": o[k],
+                    "fp32_vs_oracle_1e6": rel(f32_sub[k], o[k]),
+                    "fp64_vs_oracle_1e6": rel(f64_sub[k], o[k]),
+                    "fp32_vs_fp64_1e7": rel(f32_mid[k], f64_mid[k]),
+                    "fp32_1e9": f32_big[k]}
+        if k in ("R", "T", "A"):
+            table[k]["se_1e9"] = f32_big[k + "_se"]
+            table[k]["se_1e6"] = o[k + "_se"]
+    odepth = {"depth": o["depth"]}
+    out = {"workload": "512^3 CH mask phi=0.90 (16 MiB bricks, 1 GiB Q32.32 field), mu_s h 0.5, "
+                       "mu_a h 0.005, g 0.7", "mask_generation_s": gen_s,
+           "photons": {"subset": n_sub, "mid": n_mid, "fp32_full": n_big},
+           "ms": {"fp32_1e6": f32_sub["_ms"], "fp64_1e6": f64_sub["_ms"], "fp32_1e7": f32_mid["_ms"],
+                  "fp64_1e7": f64_mid["_ms"], "fp32_full": f32_big["_ms"],
+                  "oracle_1e6_s": oracle_s, "oracle_cores": os.cpu_count()},
+           "fp32_photons_per_s": n_big / (f32_big["_ms"] / 1e3),
+           "fp64_photons_per_s": n_mid / (f64_mid["_ms"] / 1e3),
+           "steps_per_photon": f32_big["steps"] / n_big,
+           "events_fp32_vs_oracle_1e6": {k: [f32_sub[k], o["counts"][kk]] for k, kk in
+                                        (("interactions", "interactions"), ("exit_R", "exit_R"),
+                                         ("exit_T", "exit_T"), ("rr_kill", "rr_kill"))},
+           "events_fp64_vs_oracle_1e6": {k: [f64_sub[k], o["counts"][kk]] for k, kk in
+                                        (("interactions", "interactions"), ("exit_R", "exit_R"),
+                                         ("exit_T", "exit_T"), ("rr_kill", "rr_kill"))},
+           "depth_profile_max_rel_dev": {"fp32_vs_oracle_1e6": prof_dev(f32_sub, odepth),
+                                         "fp64_vs_oracle_1e6": prof_dev(f64_sub, odepth),
+                                         "fp32_vs_fp64_1e7": prof_dev(f32_mid, f64_mid)},
+           "closure_fp32_1e9": f32_big["closure"], "identity_residual_fp32_1e9":
+               f32_big["identity_residual"], "status_fp32_1e9": f32_big["status"],
+           "results": table}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,9 +358,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batch", "paper"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch", "paper", "precision"],
                     help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
                          "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
+    ap.add_argument("--precision-photons", type=int, default=1_000_000_000)
     ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
                     help="profiling case: one warm-up launch of N/10 photons, then one timed "
                          "launch of N photons on the workload; prints its time and exits")
@@ -297,7 +378,7 @@ def main():
     import torch.distributed as dist
     from paper_2604_13929_gb300 import build as spbuild
     spbuild.build()
-    from paper_2604_13929_gb300 import spmc
+    from paper_2604_13929_gb300 import shard, spmc
 
     torch.cuda.set_device(local_rank)
     if world > 1:
@@ -313,6 +394,10 @@ def main():
     if args.workload == "paper":
         if rank == 0:
             paper_comparison(torch, spmc)
+        return
+    if args.workload == "precision":
+        if rank == 0:
+            precision_study(torch, spmc, args)
         return
     mask = make_mask("cuda")
     stream = torch.cuda.current_stream()
@@ -330,8 +415,11 @@ def main():
                           "interactions": t["interactions"]}), flush=True)
         prof.close()
         return
-    seed = SEED + rank                      # replicas: independent photon streams per rank
-    sim = spmc.Simulation(mask, MUS, MUA, G)
+    # ranks run disjoint photon-id ranges of one stream (same key), so their
+    # integer tallies would sum to one larger run; no collective on the path
+    seed = SEED
+    first_pid, _ = shard.photon_range(rank, world, args.photons * world)
+    sim = spmc.Simulation(mask, MUS, MUA, G, pid_offset=first_pid)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
     def step(ev=None):
@@ -417,7 +505,7 @@ def main():
     for i in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = spmc.Simulation(host_mask, MUS, MUA, G)
+        s2 = spmc.Simulation(host_mask, MUS, MUA, G, pid_offset=first_pid)
         s2.run(args.photons, seed, stream)
         s2.tallies(stream)
         s2.close()
@@ -436,7 +524,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "mask": "256x256x256", "porosity": POROSITY,
-                   "photons_per_step": args.photons, "parallelism": f"replicas x{world}",
+                   "photons_per_step": args.photons,
+                   "parallelism": f"photon-id shards x{world} (no collective)",
                    "l2": "flushed between steps (256 MiB write)"},
         "voxel_steps_per_s": value * steps_per_photon,
         "steps_per_photon": steps_per_photon,
