@@ -1,8 +1,13 @@
-"""Build libspmc.so in-tree with nvcc for sm_103a.
+"""Build libspmc.so and libspnn.so in-tree with nvcc for sm_103a.
 
-The translation units are compiled in parallel and linked into
-``paper_2604_13929_gb300/_lib/libspmc.so`` (static CUDA runtime, so the
-library needs only the driver at run time).  Usage::
+The translation units of both libraries are compiled in parallel and linked
+into ``paper_2604_13929_gb300/_lib/`` (static CUDA runtime, so the libraries
+need only the driver at run time):
+
+* libspmc -- the voxel Monte Carlo transport (include/spmc.h);
+* libspnn -- the fluence surrogate's tensor-core kernels (include/spnn.h).
+
+Usage::
 
     python -m paper_2604_13929_gb300.build [--verbose]
 """
@@ -20,8 +25,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libspmc.so")
+NN_LIB = os.path.join(LIBDIR, "libspnn.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["spmc_api.cu", "spmc_transport_f32.cu", "spmc_transport_f64.cu", "spmc_probe.cu"]
+NN_SOURCES = ["spnn_api.cu", "spnn_gemm.cu"]
+TARGETS = {LIB: (SOURCES, "spmc"), NN_LIB: (NN_SOURCES, "spnn")}
 # The FP64 transport evaluates the plain-definition formulas in their written
 # order; contraction into fused multiply-adds would change its rounding.
 PER_SOURCE_FLAGS = {"spmc_transport_f64.cu": ["-fmad=false"]}
@@ -42,15 +50,19 @@ def _flags(verbose: bool):
     return f
 
 
-def _deps():
-    return [os.path.join(CSRC, n) for n in os.listdir(CSRC)] + [os.path.join(INCLUDE, "spmc.h")]
+def _deps(prefix):
+    return ([os.path.join(CSRC, n) for n in os.listdir(CSRC) if n.startswith(prefix)]
+            + [os.path.join(INCLUDE, prefix + ".h")])
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    for lib, (_, prefix) in TARGETS.items():
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not all(os.path.getmtime(d) <= t for d in _deps(prefix)):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -68,17 +80,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stdout + r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    every = [src for srcs, _ in TARGETS.values() for src in srcs]
+    with cf.ThreadPoolExecutor(len(every)) as ex:
+        results = dict(zip(every, ex.map(compile_one, every)))
     if verbose:
-        for _, log in results:
+        for _, log in results.values():
             sys.stderr.write(log)
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    for lib, (srcs, _) in TARGETS.items():
+        tmp = lib + f".{os.getpid()}.tmp"
+        cmd = [cc, ARCH, "-shared", "-o", tmp, *[results[s][0] for s in srcs]]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

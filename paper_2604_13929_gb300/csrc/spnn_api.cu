@@ -1,0 +1,902 @@
+// spnn_api.cu -- C ABI of the fluence surrogate (include/spnn.h): tensor-map
+// construction, layer calls on the tensor-core GEMM kernels, weight packing,
+// data kernels and the U-Net runtime (buffers, forward, backward, Adam).
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "spnn.h"
+#include "spnn_internal.cuh"
+#include "spnn_umma.cuh"
+
+using namespace spnn;
+
+namespace {
+
+thread_local std::string g_error;
+__device__ int g_err_flag;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(SPNN_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CU(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+int* err_ptr() {
+    static int* p = nullptr;
+    if (!p) {
+        void* q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_err_flag) != cudaSuccess) return nullptr;
+        p = static_cast<int*>(q);
+    }
+    return p;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ------------------------------------------------------------ tensor maps --
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+struct Box {
+    int x, y, z, b;
+};
+
+// Box of `rows` consecutive voxels of a (B, D, H, W) grid (powers of two in
+// D, H, W): whole x-rows first, then y, z and batch.
+bool make_box(int rows, int B, int D, int H, int W, Box* box) {
+    long long total = (long long)B * D * H * W;
+    if (total % rows) return false;
+    int rem = rows;
+    box->x = W < rem ? W : rem;
+    rem /= box->x;
+    box->y = H < rem ? H : rem;
+    rem /= box->y;
+    box->z = D < rem ? D : rem;
+    rem /= box->z;
+    box->b = rem;
+    return box->b <= B && B % box->b == 0;
+}
+
+// Tensor map over a channels-last BF16 tensor of C channels whose voxel grid is
+// (B, D, H, W) with voxel strides (sx, sy, sz, sb) in elements, box (8, box).
+int encode(CUtensorMap* m, const void* base, int C, int B, int D, int H, int W, long long sx, long long sy,
+           long long sz, long long sb, const Box& box) {
+    auto fn = encode_fn();
+    if (!fn) return fail(SPNN_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    if (reinterpret_cast<uintptr_t>(base) % 16) return fail(SPNN_EINVAL, "tensor base not 16-byte aligned");
+    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    cuuint64_t strides[4] = {(cuuint64_t)(sx * 2), (cuuint64_t)(sy * 2), (cuuint64_t)(sz * 2),
+                             (cuuint64_t)(sb * 2)};
+    cuuint32_t bdim[5] = {8, (cuuint32_t)box.x, (cuuint32_t)box.y, (cuuint32_t)box.z, (cuuint32_t)box.b};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, bdim, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SPNN_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return SPNN_OK;
+}
+
+// Plain map over a (B, D, H, W, C) tensor.
+int map_plain(CUtensorMap* m, const void* p, int C, int B, int D, int H, int W, const Box& box) {
+    const long long sx = C, sy = (long long)W * C, sz = sy * H, sb = sz * D;
+    return encode(m, p, C, B, D, H, W, sx, sy, sz, sb, box);
+}
+
+// Stride-2 view of a fine (B, 2D, 2H, 2W, C) tensor at offset o = (oz, oy, ox),
+// indexed by the coarse grid (B, D, H, W).
+int map_strided(CUtensorMap* m, const void* p, int C, int B, int D, int H, int W, int o, const Box& box) {
+    const int Wf = 2 * W, Hf = 2 * H, Df = 2 * D;
+    const int oz = o >> 2, oy = (o >> 1) & 1, ox = o & 1;
+    const __nv_bfloat16* base =
+        static_cast<const __nv_bfloat16*>(p) + (((long long)oz * Hf + oy) * Wf + ox) * C;
+    const long long sx = 2LL * C, sy = 2LL * Wf * C, sz = 2LL * Hf * Wf * C, sb = (long long)Df * Hf * Wf * C;
+    return encode(m, base, C, B, D, H, W, sx, sy, sz, sb, box);
+}
+
+int n_taps_of(int kind) { return kind == KIND_CONV3 ? 27 : 8; }
+
+
+// ------------------------------------------------------------ rows GEMM --
+int rows_gemm(RowsParams& p, long long rows, cudaStream_t st) {
+    if (p.n_total <= 0 || p.n_total % 16) return fail(SPNN_EINVAL, "GEMM N %d not a multiple of 16", p.n_total);
+    p.n_tile = p.n_total <= 256 ? p.n_total : 256;
+    if (p.n_total % p.n_tile) return fail(SPNN_EINVAL, "GEMM N %d > 256 not a multiple of 256", p.n_total);
+    if (p.kc_total < 2 || p.kc_total % 2) return fail(SPNN_EINVAL, "input channels not a multiple of 16");
+    int ks = p.kc_total < 8 ? p.kc_total : 8;
+    while (p.kc_total % ks) ks -= 2;
+    p.kc_step = ks;
+    p.ksteps = p.n_taps * (p.kc_total / ks);
+    p.a_stage_bytes = 2048u * ks;
+    p.b_stage_bytes = (uint32_t)(ks * p.n_tile * 16);
+    p.stage_bytes = (p.a_stage_bytes + p.b_stage_bytes + 1023u) & ~1023u;
+    int S = (int)((100u * 1024u) / p.stage_bytes);
+    p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
+    // K-major no-swizzle operands: the leading-dimension offset is the step
+    // between 16-byte chunk planes along K (2048 for A, n_tile*16 for B), the
+    // stride-dimension offset the step between 8-row groups (128).
+    p.idesc = idesc_bf16(128, p.n_tile, 0, 0);
+    p.lbo_a = 2048;
+    p.sbo_a = 128;
+    p.lbo_b = (uint32_t)(p.n_tile * 16);
+    p.sbo_b = 128;
+    p.err = err_ptr();
+    if (!p.err) return fail(SPNN_ECUDA, "no device");
+    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
+    if (rows % kRows) return fail(SPNN_EINVAL, "rows %lld not a multiple of 128", rows);
+    cudaError_t e = launch_rows(p, (int)(rows / kRows), p.n_total / p.n_tile, smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rows_kernel launch");
+    return SPNN_OK;
+}
+
+// ----------------------------------------------------------- wgrad GEMM --
+int wgrad_gemm(WgradParams& p, int btaps, cudaStream_t st) {
+    if (p.n <= 0 || p.n % 16 || p.n > 256) return fail(SPNN_EINVAL, "wgrad N %d must be 16..256, step 16", p.n);
+    const long long vox = (long long)p.V_B * p.V_D * p.V_H * p.V_W;
+    if (vox % kWgradK) return fail(SPNN_EINVAL, "wgrad voxels not a multiple of 64");
+    p.ksteps_total = (int)(vox / kWgradK);
+    const int groups_all = p.n_groups + (p.ones_group >= 0 ? 1 : 0);
+    const int m_tiles = (groups_all + 15) / 16;
+    int splits = (4 * 152 + m_tiles * btaps - 1) / (m_tiles * btaps);
+    if (splits < 1) splits = 1;
+    if (splits > p.ksteps_total) splits = p.ksteps_total;
+    p.ksteps_per_cta = (p.ksteps_total + splits - 1) / splits;
+    splits = (p.ksteps_total + p.ksteps_per_cta - 1) / p.ksteps_per_cta;
+    p.a_stage_bytes = 16u * 1024u;
+    p.b_stage_bytes = (uint32_t)(p.n * 128);
+    p.stage_bytes = p.a_stage_bytes + p.b_stage_bytes;
+    int S = (int)((100u * 1024u) / p.stage_bytes);
+    p.stages = S < 2 ? 2 : (S > 6 ? 6 : S);
+    // MN-major no-swizzle operands: leading-dimension offset = step between
+    // 8-voxel core matrices along K (128), stride-dimension offset = step
+    // between 8-channel groups along M / N (one 1 KB box, 1024).
+    p.idesc = idesc_bf16(128, p.n, 1, 1);
+    p.lbo = 128;
+    p.sbo = 1024;
+    p.err = err_ptr();
+    if (!p.err) return fail(SPNN_ECUDA, "no device");
+    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
+    cudaError_t e = launch_wgrad(p, dim3(splits, m_tiles, btaps), smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "wgrad_kernel launch");
+    return SPNN_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// ------------------------------------------------------------- packing --
+// Packed operand element (tile, tap, kc, nn, e) with dims (n_tiles, taps_p,
+// kc_total, n_tile, 8) holds B[n = tile * n_tile + nn][k = kc * 8 + e] of the
+// GEMM for that tap; the source is the FP32 master W[t][ci][co].
+__global__ void pack_kernel(int kind, int which, int cin, int cout, int taps_p, int kc_total, int n_tile,
+                            const float* __restrict__ w, __nv_bfloat16* __restrict__ out, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long r = i;
+        const int e = (int)(r % 8);
+        r /= 8;
+        const int nn = (int)(r % n_tile);
+        r /= n_tile;
+        const int kc = (int)(r % kc_total);
+        r /= kc_total;
+        const int tap = (int)(r % taps_p);
+        const int tile = (int)(r / taps_p);
+        const int n = tile * n_tile + nn, k = kc * 8 + e;
+        int t, ci, co;
+        if (which == SPNN_PACK_FWD) {
+            if (kind == KIND_UP) {         // n = (o, co), k = ci
+                t = n / cout;
+                co = n % cout;
+                ci = k;
+            } else {                       // n = co, k = ci
+                t = tap;
+                ci = k;
+                co = n;
+            }
+        } else {
+            if (kind == KIND_CONV3) {      // n = ci, k = co, flipped taps
+                t = 26 - tap;
+                ci = n;
+                co = k;
+            } else if (kind == KIND_DOWN) {  // n = (o, ci), k = co
+                t = n / cin;
+                ci = n % cin;
+                co = k;
+            } else {                       // n = ci, k = (o, co)
+                t = tap;
+                ci = n;
+                co = k;
+            }
+        }
+        out[i] = __float2bfloat16_rn(w[((size_t)t * cin + ci) * cout + co]);
+    }
+}
+
+// GEMM geometry of a packed operand: taps in the pack, K chunks, N.
+void pack_geometry(int kind, int which, int cin, int cout, int* taps_p, int* kc_total, int* n_total) {
+    if (which == SPNN_PACK_FWD) {
+        *taps_p = kind == KIND_UP ? 1 : n_taps_of(kind);
+        *kc_total = cin / 8;
+        *n_total = kind == KIND_UP ? 8 * cout : cout;
+    } else {
+        *taps_p = kind == KIND_DOWN ? 1 : n_taps_of(kind);
+        *kc_total = cout / 8;
+        *n_total = kind == KIND_DOWN ? 8 * cin : cin;
+    }
+}
+
+int check_kind(int kind, int cin, int cout) {
+    if (kind < KIND_CONV3 || kind > KIND_UP) return fail(SPNN_EINVAL, "unknown layer kind %d", kind);
+    if (cin <= 0 || cout <= 0 || cin % 16 || cout % 16)
+        return fail(SPNN_EINVAL, "channels (%d, %d) must be positive multiples of 16", cin, cout);
+    return SPNN_OK;
+}
+
+int grid_ok(int B, int D, int H, int W) {
+    if (B <= 0 || !pow2(D) || !pow2(H) || !pow2(W))
+        return fail(SPNN_EINVAL, "grid (%d, %d, %d, %d): D, H, W must be powers of two", B, D, H, W);
+    return SPNN_OK;
+}
+
+EpiDest dest(void* out, int ld, int col0, const void* addend, const void* mask, const float* bias, int relu) {
+    EpiDest d;
+    d.out = static_cast<__nv_bfloat16*>(out);
+    d.addend = static_cast<const __nv_bfloat16*>(addend);
+    d.mask = static_cast<const __nv_bfloat16*>(mask);
+    d.bias = bias;
+    d.ld = ld;
+    d.col0 = col0;
+    d.relu = relu;
+    return d;
+}
+
+int layer_forward(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
+                  const void* packed, const float* bias, int cout, int relu, void* y, const float* head_w,
+                  const float* head_b, float* head_out, cudaStream_t st) {
+    int rc;
+    if ((rc = check_kind(kind, c0 + c1, cout)) || (rc = grid_ok(B, D, H, W))) return rc;
+    if (!x0 || !packed || !y || (c1 && !x1)) return fail(SPNN_EINVAL, "null tensor");
+    if (c1 && kind != KIND_CONV3) return fail(SPNN_EINVAL, "concatenated input only for conv3");
+    if (c0 % 8 || c1 % 8) return fail(SPNN_EINVAL, "source channels must be multiples of 8");
+    if (kind == KIND_DOWN && (D < 2 || H < 2 || W < 2)) return fail(SPNN_EINVAL, "down needs D, H, W >= 2");
+    if (head_out && (kind != KIND_CONV3 || cout > 256 || !head_w || !head_b))
+        return fail(SPNN_EINVAL, "fused head needs conv3, cout <= 256, head_w and head_b");
+    RowsParams p;
+    memset(&p, 0, sizeof p);
+    int RD = D, RH = H, RW = W;
+    if (kind == KIND_DOWN) {
+        RD /= 2;
+        RH /= 2;
+        RW /= 2;
+    }
+    Box box;
+    if (!make_box(kRows, B, RD, RH, RW, &box))
+        return fail(SPNN_EINVAL, "row grid (%d, %d, %d, %d) does not tile into 128-voxel boxes", B, RD, RH, RW);
+    if (kind == KIND_CONV3) {
+        p.tap_mode = TAP_SHIFT3;
+        p.n_taps = 27;
+        if ((rc = map_plain(&p.maps[0], x0, c0, B, D, H, W, box))) return rc;
+        if (c1 && (rc = map_plain(&p.maps[1], x1, c1, B, D, H, W, box))) return rc;
+    } else if (kind == KIND_DOWN) {
+        p.tap_mode = TAP_MAP;
+        p.n_taps = 8;
+        for (int o = 0; o < 8; ++o)
+            if ((rc = map_strided(&p.maps[o], x0, c0, B, RD, RH, RW, o, box))) return rc;
+    } else {
+        p.tap_mode = TAP_NONE;
+        p.n_taps = 1;
+        if ((rc = map_plain(&p.maps[0], x0, c0, B, D, H, W, box))) return rc;
+    }
+    p.kc_total = (c0 + c1) / 8;
+    p.kc0 = c0 / 8;
+    p.wpack = static_cast<const __nv_bfloat16*>(packed);
+    p.R_B = B;
+    p.R_D = RD;
+    p.R_H = RH;
+    p.R_W = RW;
+    p.n_total = kind == KIND_UP ? 8 * cout : cout;
+    p.scatter_up = kind == KIND_UP;
+    p.cout_up = cout;
+    p.split = p.n_total;
+    p.d[0] = dest(y, cout, 0, nullptr, nullptr, bias, relu);
+    p.d[1] = p.d[0];
+    p.head_out = head_out;
+    p.head_w = head_w;
+    p.head_b = head_b;
+    return rows_gemm(p, (long long)B * RD * RH * RW, st);
+}
+
+int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, const void* packed, int c0,
+                int c1, void* dx0, const void* add0, const void* mask0, void* dx1, const void* add1,
+                const void* mask1, cudaStream_t st) {
+    int rc;
+    if ((rc = check_kind(kind, c0 + c1, cout)) || (rc = grid_ok(B, D, H, W))) return rc;
+    if (!dy || !packed || !dx0 || (c1 && !dx1)) return fail(SPNN_EINVAL, "null tensor");
+    if (c1 && kind != KIND_CONV3) return fail(SPNN_EINVAL, "split input gradient only for conv3");
+    RowsParams p;
+    memset(&p, 0, sizeof p);
+    Box box;
+    if (kind == KIND_CONV3) {
+        if (!make_box(kRows, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 128 rows");
+        if ((rc = map_plain(&p.maps[0], dy, cout, B, D, H, W, box))) return rc;
+        p.tap_mode = TAP_SHIFT3;
+        p.n_taps = 27;
+        p.R_B = B, p.R_D = D, p.R_H = H, p.R_W = W;
+        p.n_total = c0 + c1;
+        p.split = c0;
+        p.d[0] = dest(dx0, c0, 0, add0, mask0, nullptr, 0);
+        p.d[1] = c1 ? dest(dx1, c1, c0, add1, mask1, nullptr, 0) : p.d[0];
+    } else if (kind == KIND_DOWN) {
+        const int RD = D / 2, RH = H / 2, RW = W / 2;
+        if (!make_box(kRows, B, RD, RH, RW, &box)) return fail(SPNN_EINVAL, "grid does not tile into 128 rows");
+        if ((rc = map_plain(&p.maps[0], dy, cout, B, RD, RH, RW, box))) return rc;
+        p.tap_mode = TAP_NONE;
+        p.n_taps = 1;
+        p.R_B = B, p.R_D = RD, p.R_H = RH, p.R_W = RW;
+        p.n_total = 8 * c0;
+        p.split = p.n_total;
+        p.scatter_up = 1;
+        p.cout_up = c0;
+        p.d[0] = dest(dx0, c0, 0, add0, mask0, nullptr, 0);
+        p.d[1] = p.d[0];
+    } else {
+        if (!make_box(kRows, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 128 rows");
+        for (int o = 0; o < 8; ++o)
+            if ((rc = map_strided(&p.maps[o], dy, cout, B, D, H, W, o, box))) return rc;
+        p.tap_mode = TAP_MAP;
+        p.n_taps = 8;
+        p.R_B = B, p.R_D = D, p.R_H = H, p.R_W = W;
+        p.n_total = c0;
+        p.split = c0;
+        p.d[0] = dest(dx0, c0, 0, add0, mask0, nullptr, 0);
+        p.d[1] = p.d[0];
+    }
+    p.kc_total = cout / 8;
+    p.kc0 = p.kc_total;
+    p.wpack = static_cast<const __nv_bfloat16*>(packed);
+    return rows_gemm(p, (long long)p.R_B * p.R_D * p.R_H * p.R_W, st);
+}
+
+int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
+                const void* dy, int cout, float* dw, float* db, cudaStream_t st) {
+    int rc;
+    if ((rc = check_kind(kind, c0 + c1, cout)) || (rc = grid_ok(B, D, H, W))) return rc;
+    if (!x0 || !dy || !dw || (c1 && !x1)) return fail(SPNN_EINVAL, "null tensor");
+    if (c1 && kind != KIND_CONV3) return fail(SPNN_EINVAL, "concatenated input only for conv3");
+    if (c0 % 8 || c1 % 8) return fail(SPNN_EINVAL, "source channels must be multiples of 8");
+    WgradParams p;
+    memset(&p, 0, sizeof p);
+    p.mode = kind;
+    p.kc_total = (c0 + c1) / 8;
+    p.kc0 = c0 / 8;
+    p.n = cout;
+    p.dw = dw;
+    p.db = db;
+    Box box;
+    int btaps = 1;
+    if (kind == KIND_CONV3) {
+        p.V_B = B, p.V_D = D, p.V_H = H, p.V_W = W;
+        if (!make_box(kWgradK, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 64 voxels");
+        if ((rc = map_plain(&p.amaps[0], x0, c0, B, D, H, W, box))) return rc;
+        if (c1 && (rc = map_plain(&p.amaps[1], x1, c1, B, D, H, W, box))) return rc;
+        if ((rc = map_plain(&p.bmaps[0], dy, cout, B, D, H, W, box))) return rc;
+        p.n_groups = 27 * p.kc_total;
+    } else if (kind == KIND_DOWN) {
+        const int RD = D / 2, RH = H / 2, RW = W / 2;
+        p.V_B = B, p.V_D = RD, p.V_H = RH, p.V_W = RW;
+        if (!make_box(kWgradK, B, RD, RH, RW, &box)) return fail(SPNN_EINVAL, "grid does not tile into 64 voxels");
+        for (int o = 0; o < 8; ++o)
+            if ((rc = map_strided(&p.amaps[o], x0, c0, B, RD, RH, RW, o, box))) return rc;
+        if ((rc = map_plain(&p.bmaps[0], dy, cout, B, RD, RH, RW, box))) return rc;
+        p.n_groups = 8 * p.kc_total;
+    } else {
+        p.V_B = B, p.V_D = D, p.V_H = H, p.V_W = W;
+        if (!make_box(kWgradK, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 64 voxels");
+        if ((rc = map_plain(&p.amaps[0], x0, c0, B, D, H, W, box))) return rc;
+        for (int o = 0; o < 8; ++o)
+            if ((rc = map_strided(&p.bmaps[o], dy, cout, B, D, H, W, o, box))) return rc;
+        p.n_groups = p.kc_total;
+        btaps = 8;
+    }
+    p.ones_group = db ? p.n_groups : -1;
+    return wgrad_gemm(p, btaps, st);
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// --------------------------------------------------------- data kernels --
+__global__ void pack_input_kernel(const uint8_t* __restrict__ mask, const float* __restrict__ optics, int D,
+                                  long long vox_per_sample, long long total, __nv_bfloat16* __restrict__ x,
+                                  int HW) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / vox_per_sample;
+        const int z = (int)((i % vox_per_sample) / HW);
+        const float pore = mask[i] ? 1.f : 0.f;
+        const float mus = optics[3 * b], mua = optics[3 * b + 1], g = optics[3 * b + 2];
+        float f[16] = {pore, 1.f - pore, logf(mus), 0.25f * logf(mua), g, (z + 0.5f) / (float)D};
+        uint4 w[2];
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+        uint4* dst = reinterpret_cast<uint4*>(x + i * 16);
+        dst[0] = w[0];
+        dst[1] = w[1];
+    }
+}
+
+__global__ void log_fluence_kernel(const uint64_t* __restrict__ raw, const double* __restrict__ n_photons,
+                                   long long vox_per_sample, long long total, double area, float floor_,
+                                   float* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double n = n_photons[i / vox_per_sample];
+        const double phi = (double)raw[i] * (area / (n * 4294967296.0));
+        out[i] = logf(fmaxf((float)phi, floor_));
+    }
+}
+
+// one block per (sample, z layer): sums of exp(log_phi) per phase
+__global__ void phase_profile_kernel(const float* __restrict__ log_phi, const uint8_t* __restrict__ mask, int HW,
+                                     float* __restrict__ prof, int D) {
+    const long long base = (long long)blockIdx.x * HW;
+    float s[2] = {0.f, 0.f};
+    int c[2] = {0, 0};
+    for (int i = threadIdx.x; i < HW; i += blockDim.x) {
+        const int ph = mask[base + i] ? 1 : 0;
+        s[ph] += expf(log_phi[base + i]);
+        c[ph] += 1;
+    }
+    __shared__ float ss[2][32];
+    __shared__ int cc[2][32];
+    for (int ph = 0; ph < 2; ++ph) {
+        for (int o = 16; o; o >>= 1) {
+            s[ph] += __shfl_xor_sync(0xffffffffu, s[ph], o);
+            c[ph] += __shfl_xor_sync(0xffffffffu, c[ph], o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            ss[ph][threadIdx.x >> 5] = s[ph];
+            cc[ph][threadIdx.x >> 5] = c[ph];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int ph = threadIdx.x;
+        float t = 0.f;
+        int n = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += ss[ph][w];
+            n += cc[ph][w];
+        }
+        const int b = blockIdx.x / D, z = blockIdx.x % D;
+        prof[((long long)b * 2 + ph) * D + z] = n ? t / n : __int_as_float(0x7fc00000);
+    }
+}
+
+// Loss and head backward, one thread per voxel: d = pred - target,
+// loss += d^2 / n, dp = 2 d / n; g[v, c] = dp h[c] (a[v, c] > 0);
+// dh[c] += dp a[v, c]; dc += dp.
+template <int C>
+__global__ void loss_head_kernel(const float* __restrict__ pred, const float* __restrict__ target,
+                                 const __nv_bfloat16* __restrict__ act, const float* __restrict__ hw,
+                                 long long total, double inv_n, double* loss, __nv_bfloat16* __restrict__ g,
+                                 float* __restrict__ dhw, float* __restrict__ dhb) {
+    __shared__ float sh[C + 1];
+    __shared__ double sl;
+    if (threadIdx.x <= C) sh[threadIdx.x] = 0.f;
+    if (threadIdx.x == 0) sl = 0.0;
+    __syncthreads();
+    float acc[C + 1];
+#pragma unroll
+    for (int c = 0; c <= C; ++c) acc[c] = 0.f;
+    double l = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double d = (double)pred[i] - (double)target[i];
+        l += d * d;
+        const float dp = (float)(2.0 * d * inv_n);
+        acc[C] += dp;
+#pragma unroll
+        for (int c0 = 0; c0 < C; c0 += 8) {
+            const uint4 u = *reinterpret_cast<const uint4*>(act + i * C + c0);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+            uint4 o;
+            __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 a = __bfloat1622float2(h[k]);
+                const int c = c0 + 2 * k;
+                acc[c] += dp * a.x;
+                acc[c + 1] += dp * a.y;
+                oh[k] = __floats2bfloat162_rn(a.x > 0.f ? dp * hw[c] : 0.f, a.y > 0.f ? dp * hw[c + 1] : 0.f);
+            }
+            *reinterpret_cast<uint4*>(g + i * C + c0) = o;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c <= C; ++c) {
+        float v = acc[c];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sh[c], v);
+    }
+    for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sl, l);
+    __syncthreads();
+    if (threadIdx.x < C) atomicAdd(&dhw[threadIdx.x], sh[threadIdx.x]);
+    if (threadIdx.x == C) atomicAdd(dhb, sh[C]);
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, sl * inv_n);
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+int grid_for(long long n, int threads = 256) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+}
+
+int pack(int kind, int cin, int cout, int which, const float* w, void* packed, cudaStream_t st) {
+    int rc;
+    if ((rc = check_kind(kind, cin, cout))) return rc;
+    if (!w || !packed) return fail(SPNN_EINVAL, "null tensor");
+    int taps_p, kc, n_total;
+    pack_geometry(kind, which, cin, cout, &taps_p, &kc, &n_total);
+    const int n_tile = n_total <= 256 ? n_total : 256;
+    if (n_total % n_tile) return fail(SPNN_EINVAL, "packed N %d > 256 not a multiple of 256", n_total);
+    const long long total = (long long)taps_p * kc * 8 * n_total;
+    pack_kernel<<<grid_for(total), 256, 0, st>>>(kind, which, cin, cout, taps_p, kc, n_tile, w,
+                                                  static_cast<__nv_bfloat16*>(packed), total);
+    CU(cudaGetLastError());
+    return SPNN_OK;
+}
+
+}  // namespace
+
+// ================================================================ U-Net ==
+struct spnn_unet {
+    struct Layer {
+        int kind, cin, cout, relu, src0, src1, edge_in, edge_out, taps;
+        size_t woff, boff;
+        __nv_bfloat16 *pk_fwd = nullptr, *pk_dgrad = nullptr;
+        __nv_bfloat16 *act = nullptr, *grad = nullptr;
+    };
+    int c0 = 0, n = 0, max_batch = 0, adam_t = 0;
+    std::vector<Layer> L;
+    size_t nparam = 0, head_w = 0, head_b = 0;
+    float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    const void* last_x = nullptr;
+    float* last_pred = nullptr;
+    int last_batch = 0;
+};
+
+namespace {
+
+constexpr int kLayers = 20;
+// source layer indices (-1 = network input), decoder "a" layers read [up, skip]
+const int kSrc0[kLayers] = {-1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18};
+const int kSrc1[kLayers] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 7, -1, -1, 4, -1, -1, 1, -1};
+const int kKind[kLayers] = {0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 2, 0, 0, 2, 0, 0, 2, 0, 0};
+const int kLevel[kLayers] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0};  // of the input
+const int kCoutMul[kLayers] = {1, 1, 2, 2, 2, 4, 4, 4, 8, 8, 8, 4, 4, 4, 2, 2, 2, 1, 1, 1};
+
+void free_net(spnn_unet* net) {
+    if (!net) return;
+    for (auto& l : net->L) {
+        cudaFree(l.pk_fwd);
+        cudaFree(l.pk_dgrad);
+        cudaFree(l.act);
+        cudaFree(l.grad);
+    }
+    cudaFree(net->params);
+    cudaFree(net->grads);
+    cudaFree(net->m);
+    cudaFree(net->v);
+    delete net;
+}
+
+int repack(spnn_unet* net, cudaStream_t st) {
+    int rc;
+    for (auto& l : net->L) {
+        if ((rc = pack(l.kind, l.cin, l.cout, SPNN_PACK_FWD, net->params + l.woff, l.pk_fwd, st))) return rc;
+        if ((rc = pack(l.kind, l.cin, l.cout, SPNN_PACK_DGRAD, net->params + l.woff, l.pk_dgrad, st))) return rc;
+    }
+    return SPNN_OK;
+}
+
+int src_channels(const spnn_unet* net, int s) { return s < 0 ? 16 : net->L[s].cout; }
+
+}  // namespace
+
+// ============================================================ C ABI ==
+extern "C" {
+
+const char* spnn_last_error(void) { return g_error.c_str(); }
+int spnn_version(void) { return 1; }
+
+int spnn_status(void* stream) {
+    CU(cudaStreamSynchronize(as_stream(stream)));
+    int* e = err_ptr();
+    if (!e) return fail(SPNN_ECUDA, "no device");
+    int h = 0;
+    CU(cudaMemcpy(&h, e, sizeof h, cudaMemcpyDeviceToHost));
+    if (h) {
+        CU(cudaMemset(e, 0, sizeof h));
+        return fail(SPNN_ECUDA, "a kernel gave up on a bounded wait (flag %d)", h);
+    }
+    return SPNN_OK;
+}
+
+size_t spnn_packed_elems(int kind, int cin, int cout) {
+    return (size_t)(kind == KIND_CONV3 ? 27 : 8) * cin * cout;
+}
+
+int spnn_pack_weights(int kind, int cin, int cout, int which, const float* w, void* packed, void* stream) {
+    return pack(kind, cin, cout, which, w, packed, as_stream(stream));
+}
+
+int spnn_layer_forward(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
+                       const void* packed, const float* bias, int cout, int relu, void* y, const float* head_w,
+                       const float* head_b, float* head_out, void* stream) {
+    return layer_forward(kind, B, D, H, W, x0, c0, x1, c1, packed, bias, cout, relu, y, head_w, head_b, head_out,
+                         as_stream(stream));
+}
+
+int spnn_layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, const void* packed, int c0,
+                     int c1, void* dx0, const void* addend0, const void* mask0, void* dx1, const void* addend1,
+                     const void* mask1, void* stream) {
+    return layer_dgrad(kind, B, D, H, W, dy, cout, packed, c0, c1, dx0, addend0, mask0, dx1, addend1, mask1,
+                       as_stream(stream));
+}
+
+int spnn_layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
+                     const void* dy, int cout, float* dw, float* db, void* stream) {
+    return layer_wgrad(kind, B, D, H, W, x0, c0, x1, c1, dy, cout, dw, db, as_stream(stream));
+}
+
+int spnn_pack_input(const uint8_t* mask, const float* optics, int B, int D, int H, int W, void* x, void* stream) {
+    if (!mask || !optics || !x || B <= 0 || D <= 0 || H <= 0 || W <= 0) return fail(SPNN_EINVAL, "bad arguments");
+    const long long vps = (long long)D * H * W, total = vps * B;
+    pack_input_kernel<<<grid_for(total), 256, 0, as_stream(stream)>>>(mask, optics, D, vps, total,
+                                                                       static_cast<__nv_bfloat16*>(x), H * W);
+    CU(cudaGetLastError());
+    return SPNN_OK;
+}
+
+int spnn_log_fluence(const uint64_t* raw, const double* n_photons, int B, int D, int H, int W, float floor_,
+                     float* out, void* stream) {
+    if (!raw || !n_photons || !out || B <= 0 || D <= 0 || H <= 0 || W <= 0 || !(floor_ > 0.f))
+        return fail(SPNN_EINVAL, "bad arguments");
+    const long long vps = (long long)D * H * W, total = vps * B;
+    log_fluence_kernel<<<grid_for(total), 256, 0, as_stream(stream)>>>(raw, n_photons, vps, total,
+                                                                        (double)W * H, floor_, out);
+    CU(cudaGetLastError());
+    return SPNN_OK;
+}
+
+int spnn_phase_profiles(const float* log_phi, const uint8_t* mask, int B, int D, int H, int W, float* prof,
+                        void* stream) {
+    if (!log_phi || !mask || !prof || B <= 0 || D <= 0 || H <= 0 || W <= 0) return fail(SPNN_EINVAL, "bad arguments");
+    phase_profile_kernel<<<B * D, 256, 0, as_stream(stream)>>>(log_phi, mask, H * W, prof, D);
+    CU(cudaGetLastError());
+    return SPNN_OK;
+}
+
+spnn_unet_t* spnn_unet_create(int c0, int n, int max_batch) {
+    if ((c0 != 16 && c0 != 32) || !pow2(n) || n < 16 || max_batch <= 0) {
+        fail(SPNN_EINVAL, "c0 must be 16 or 32, n a power of two >= 16, max_batch > 0");
+        return nullptr;
+    }
+    auto* net = new spnn_unet;
+    net->c0 = c0;
+    net->n = n;
+    net->max_batch = max_batch;
+    size_t off = 0;
+    for (int i = 0; i < kLayers; ++i) {
+        spnn_unet::Layer l;
+        l.kind = kKind[i];
+        l.src0 = kSrc0[i];
+        l.src1 = kSrc1[i];
+        l.cout = kCoutMul[i] * c0;
+        l.cin = (l.src0 < 0 ? 16 : net->L[l.src0].cout) + (l.src1 < 0 ? 0 : net->L[l.src1].cout);
+        l.relu = l.kind != KIND_UP;
+        l.edge_in = n >> kLevel[i];
+        l.edge_out = l.kind == KIND_DOWN ? l.edge_in / 2 : (l.kind == KIND_UP ? l.edge_in * 2 : l.edge_in);
+        l.taps = n_taps_of(l.kind);
+        l.woff = off;
+        off += (size_t)l.taps * l.cin * l.cout;
+        l.boff = off;
+        off += l.cout;
+        net->L.push_back(l);
+    }
+    net->head_w = off;
+    off += c0;
+    net->head_b = off;
+    off += 1;
+    net->nparam = off;
+    bool ok = cudaMalloc(&net->params, off * 4) == cudaSuccess && cudaMalloc(&net->grads, off * 4) == cudaSuccess &&
+              cudaMalloc(&net->m, off * 4) == cudaSuccess && cudaMalloc(&net->v, off * 4) == cudaSuccess;
+    for (auto& l : net->L) {
+        if (!ok) break;
+        const size_t pe = spnn_packed_elems(l.kind, l.cin, l.cout) * 2;
+        const size_t ae = (size_t)max_batch * l.edge_out * l.edge_out * l.edge_out * l.cout * 2;
+        ok = cudaMalloc(&l.pk_fwd, pe) == cudaSuccess && cudaMalloc(&l.pk_dgrad, pe) == cudaSuccess &&
+             cudaMalloc(&l.act, ae) == cudaSuccess && cudaMalloc(&l.grad, ae) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        free_net(net);
+        fail(SPNN_ENOMEM, "device allocation failed");
+        return nullptr;
+    }
+    cudaMemset(net->params, 0, off * 4);
+    cudaMemset(net->grads, 0, off * 4);
+    cudaMemset(net->m, 0, off * 4);
+    cudaMemset(net->v, 0, off * 4);
+    return net;
+}
+
+void spnn_unet_destroy(spnn_unet_t* net) { free_net(net); }
+
+size_t spnn_unet_param_count(const spnn_unet_t* net) { return net ? net->nparam : 0; }
+
+int spnn_unet_set_params(spnn_unet_t* net, const float* params) {
+    if (!net || !params) return fail(SPNN_EINVAL, "null argument");
+    CU(cudaMemcpy(net->params, params, net->nparam * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemset(net->m, 0, net->nparam * 4));
+    CU(cudaMemset(net->v, 0, net->nparam * 4));
+    net->adam_t = 0;
+    int rc = repack(net, nullptr);
+    if (rc) return rc;
+    CU(cudaDeviceSynchronize());
+    return SPNN_OK;
+}
+
+int spnn_unet_get_params(spnn_unet_t* net, float* params) {
+    if (!net || !params) return fail(SPNN_EINVAL, "null argument");
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(params, net->params, net->nparam * 4, cudaMemcpyDeviceToHost));
+    return SPNN_OK;
+}
+
+int spnn_unet_get_grads(spnn_unet_t* net, float* grads) {
+    if (!net || !grads) return fail(SPNN_EINVAL, "null argument");
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(grads, net->grads, net->nparam * 4, cudaMemcpyDeviceToHost));
+    return SPNN_OK;
+}
+
+int spnn_unet_copy_activation(spnn_unet_t* net, int layer, int batch, void* dst, void* stream) {
+    if (!net || !dst || layer < 0 || layer >= kLayers || batch <= 0 || batch > net->max_batch)
+        return fail(SPNN_EINVAL, "bad arguments");
+    const auto& l = net->L[layer];
+    const size_t bytes = (size_t)batch * l.edge_out * l.edge_out * l.edge_out * l.cout * 2;
+    CU(cudaMemcpyAsync(dst, l.act, bytes, cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return SPNN_OK;
+}
+
+int spnn_unet_layer_shape(const spnn_unet_t* net, int layer, int* edge, int* channels) {
+    if (!net || !edge || !channels || layer < 0 || layer >= kLayers) return fail(SPNN_EINVAL, "bad arguments");
+    *edge = net->L[layer].edge_out;
+    *channels = net->L[layer].cout;
+    return SPNN_OK;
+}
+
+int spnn_unet_forward(spnn_unet_t* net, const void* x, int batch, float* pred, void* stream) {
+    if (!net || !x || !pred || batch <= 0 || batch > net->max_batch) return fail(SPNN_EINVAL, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    for (int i = 0; i < kLayers; ++i) {
+        auto& l = net->L[i];
+        const void* x0 = l.src0 < 0 ? x : net->L[l.src0].act;
+        const void* x1 = l.src1 < 0 ? nullptr : net->L[l.src1].act;
+        const int c0 = src_channels(net, l.src0), c1 = l.src1 < 0 ? 0 : net->L[l.src1].cout;
+        const bool last = i == kLayers - 1;
+        const int e = l.edge_in;
+        int rc = layer_forward(l.kind, batch, e, e, e, x0, c0, x1, c1, l.pk_fwd, net->params + l.boff, l.cout,
+                               l.relu, l.act, last ? net->params + net->head_w : nullptr,
+                               last ? net->params + net->head_b : nullptr, last ? pred : nullptr, st);
+        if (rc) return rc;
+    }
+    net->last_x = x;
+    net->last_pred = pred;
+    net->last_batch = batch;
+    return SPNN_OK;
+}
+
+int spnn_unet_backward(spnn_unet_t* net, const float* target, int batch, double* loss, void* stream) {
+    if (!net || !target || batch != net->last_batch || !net->last_pred)
+        return fail(SPNN_EINVAL, "backward needs the forward of the same batch first");
+    cudaStream_t st = as_stream(stream);
+    CU(cudaMemsetAsync(net->grads, 0, net->nparam * 4, st));
+    auto& last = net->L[kLayers - 1];
+    const long long vox = (long long)batch * net->n * net->n * net->n;
+    const double inv_n = 1.0 / (double)vox;
+    const int blocks = grid_for(vox, 256);
+    if (net->c0 == 16)
+        loss_head_kernel<16><<<blocks, 256, 0, st>>>(net->last_pred, target, last.act, net->params + net->head_w,
+                                                     vox, inv_n, loss, last.grad, net->grads + net->head_w,
+                                                     net->grads + net->head_b);
+    else
+        loss_head_kernel<32><<<blocks, 256, 0, st>>>(net->last_pred, target, last.act, net->params + net->head_w,
+                                                     vox, inv_n, loss, last.grad, net->grads + net->head_w,
+                                                     net->grads + net->head_b);
+    CU(cudaGetLastError());
+    for (int i = kLayers - 1; i >= 0; --i) {
+        auto& l = net->L[i];
+        const int e = l.edge_in;
+        const void* x0 = l.src0 < 0 ? net->last_x : net->L[l.src0].act;
+        const void* x1 = l.src1 < 0 ? nullptr : net->L[l.src1].act;
+        const int c0 = src_channels(net, l.src0), c1 = l.src1 < 0 ? 0 : net->L[l.src1].cout;
+        int rc = layer_wgrad(l.kind, batch, e, e, e, x0, c0, x1, c1, l.grad, l.cout, net->grads + l.woff,
+                             net->grads + l.boff, st);
+        if (rc) return rc;
+        if (i == 0) continue;
+        if (l.src1 >= 0) {
+            // [up, skip]: raw gradient of the up output; partial gradient of the skip
+            rc = layer_dgrad(l.kind, batch, e, e, e, l.grad, l.cout, l.pk_dgrad, c0, c1, net->L[l.src0].grad,
+                             nullptr, nullptr, net->L[l.src1].grad, nullptr, nullptr, st);
+        } else {
+            auto& s = net->L[l.src0];
+            // a down layer reading a skip completes the skip's gradient in place
+            const bool skip = l.kind == KIND_DOWN && (l.src0 == 1 || l.src0 == 4 || l.src0 == 7);
+            rc = layer_dgrad(l.kind, batch, e, e, e, l.grad, l.cout, l.pk_dgrad, c0, 0, s.grad,
+                             skip ? s.grad : nullptr, s.relu ? s.act : nullptr, nullptr, nullptr, nullptr, st);
+        }
+        if (rc) return rc;
+    }
+    return SPNN_OK;
+}
+
+int spnn_unet_adam(spnn_unet_t* net, float lr, float beta1, float beta2, float eps, void* stream) {
+    if (!net) return fail(SPNN_EINVAL, "null network");
+    cudaStream_t st = as_stream(stream);
+    net->adam_t += 1;
+    const double c1 = 1.0 / (1.0 - pow((double)beta1, net->adam_t));
+    const double c2 = 1.0 / (1.0 - pow((double)beta2, net->adam_t));
+    adam_kernel<<<grid_for((long long)net->nparam), 256, 0, st>>>(net->params, net->grads, net->m, net->v,
+                                                                   net->nparam, lr, beta1, beta2, eps, (float)c1,
+                                                                   (float)c2);
+    CU(cudaGetLastError());
+    return repack(net, st);
+}
+
+}  // extern "C"

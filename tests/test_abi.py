@@ -80,3 +80,34 @@ def test_product_code_never_uses_the_oracle():
                 assert not pat.search(open(os.path.join(root, f)).read()), f
     out = subprocess.run(["nm", "-D", spmc.LIB_PATH], capture_output=True, text=True).stdout
     assert "or_run" not in out and "or_philox" not in out
+
+
+@pytest.fixture(scope="module")
+def nnlib():
+    if shutil.which("nvcc") is None and not build.up_to_date():
+        pytest.skip("nvcc not available to build libspnn")
+    build.build()
+    from paper_2604_13929_gb300 import spnn
+    return spnn.load()
+
+
+def test_surrogate_library_exports_every_declared_function(nnlib):
+    from paper_2604_13929_gb300 import spnn
+    declared = spnn.declared_symbols()
+    assert len(declared) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", spnn.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (spnn_\w+)", out))
+    assert set(declared) <= exported, set(declared) - exported
+
+
+def test_surrogate_rejects_bad_shapes_before_device_work(nnlib):
+    from paper_2604_13929_gb300 import spnn
+    assert nnlib.spnn_unet_create(24, 64, 4) is None          # c0 must be 16 or 32
+    assert "c0" in nnlib.spnn_last_error().decode()
+    assert nnlib.spnn_unet_create(32, 48, 4) is None          # n must be a power of two
+    # channel counts must be multiples of 16; checked before any launch
+    assert nnlib.spnn_pack_weights(0, 24, 32, 0, None, None, None) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_layer_forward(0, 1, 8, 8, 8, None, 16, None, 0, None, None, 32, 1, None,
+                                    None, None, None, None) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_layer_wgrad(1, 1, 8, 8, 8, None, 16, None, 0, None, 32, None, None, None) == spnn.SPNN_EINVAL
