@@ -11,9 +11,10 @@
  *   down   2x2x2, stride 2; taps o = (oz, oy, ox) in {0,1}^3, index oz*4+oy*2+ox
  *   up     transposed 2x2x2, stride 2: y[2v + o] = b + x[v] W[o]
  *
- * Layout: activations are BF16, channels-last (B, D, H, W, C), x fastest
- * after C; every channel count is a multiple of 16 and every spatial extent
- * a power of two.  Master weights are FP32 W[taps][cin][cout]; the kernels
+ * Layout: activations are BF16 in "chunk planes" [C/8][B][D][H][W][8]: each
+ * plane holds 8 channels of every voxel (16 bytes per voxel, x fastest), so
+ * runs of voxels are contiguous for the TMA loads.  Every channel count is
+ * a multiple of 16 and every spatial extent a power of two.  Master weights are FP32 W[taps][cin][cout]; the kernels
  * read them through BF16 "packed" copies made by spnn_pack_weights.
  * Arithmetic: BF16 operands, FP32 accumulation on the tensor cores
  * (tcgen05, accumulators in TMEM), BF16 layer outputs, FP32 weight
@@ -105,8 +106,9 @@ int spnn_layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c
 /* ---------------------------------------------------------------- data -- */
 
 /*
- * Input features, BF16 (B, D, H, W, 16): 0 pore (mask == 1), 1 solid,
- * 2 ln(mu_s h), 3 ln(mu_a h)/4, 4 g, 5 (z + 1/2)/D, 6..15 zero.
+ * Input features, BF16 chunk planes [2][B][D][H][W][8] (16 channels):
+ * 0 pore (mask == 1), 1 solid, 2 ln(mu_s h), 3 ln(mu_a h)/4, 4 g,
+ * 5 (z + 1/2)/D, 6..15 zero.
  * mask: uint8 (B, D, H, W), 1 = pore;  optics: FP32 (B, 3) = (mu_s h, mu_a h, g).
  */
 int spnn_pack_input(const uint8_t* mask, const float* optics, int B, int D, int H, int W, void* x, void* stream);
@@ -149,7 +151,7 @@ int spnn_unet_set_params(spnn_unet_t* net, const float* params);
 int spnn_unet_get_params(spnn_unet_t* net, float* params);
 /* grads: host FP32 [param_count], from the last spnn_unet_backward. */
 int spnn_unet_get_grads(spnn_unet_t* net, float* grads);
-/* Forward of `batch` samples: x BF16 (batch, n, n, n, 16) device; pred FP32 (batch, n^3) device. */
+/* Forward of `batch` samples: x BF16 chunk planes [2][batch][n][n][n][8]; pred FP32 (batch, n^3). */
 int spnn_unet_forward(spnn_unet_t* net, const void* x, int batch, float* pred, void* stream);
 /*
  * Backward of the last forward (same x, same batch): loss = mean (pred -
@@ -161,8 +163,8 @@ int spnn_unet_backward(spnn_unet_t* net, const float* target, int batch, double*
 /* One Adam step (Kingma and Ba 2015) on the gradient buffer, then repack. */
 int spnn_unet_adam(spnn_unet_t* net, float lr, float beta1, float beta2, float eps, void* stream);
 /*
- * Copy the BF16 output of a layer (index in the order above) for the first
- * `batch` samples of the last forward into dst (device, batch * e^3 * cout).
+ * Copy the BF16 output of a layer (index in the order above) of the last
+ * forward's `batch` samples into dst (device, chunk planes [cout/8][batch][e][e][e][8]).
  */
 int spnn_unet_copy_activation(spnn_unet_t* net, int layer, int batch, void* dst, void* stream);
 /* Shape of a layer's output: edge e and channels. */

@@ -67,93 +67,125 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-struct Box {
-    int x, y, z, b;
-};
-
-// Box of `rows` consecutive voxels of a (B, D, H, W) grid (powers of two in
-// D, H, W): whole x-rows first, then y, z and batch.
-bool make_box(int rows, int B, int D, int H, int W, Box* box) {
-    long long total = (long long)B * D * H * W;
-    if (total % rows) return false;
+// Tiles of `rows` voxels over a (B, D, H, W) grid with power-of-two extents:
+// x-runs of at most 32 voxels (a 512-byte TMA box row), then y, z, samples.
+bool make_grid(int rows, int B, int D, int H, int W, TileGrid* g) {
     int rem = rows;
-    box->x = W < rem ? W : rem;
-    rem /= box->x;
-    box->y = H < rem ? H : rem;
-    rem /= box->y;
-    box->z = D < rem ? D : rem;
-    rem /= box->z;
-    box->b = rem;
-    return box->b <= B && B % box->b == 0;
+    g->B = B, g->D = D, g->H = H, g->W = W;
+    g->bx = W < 32 ? W : 32;
+    if (g->bx > rem) g->bx = rem;
+    rem /= g->bx;
+    g->by = H < rem ? H : rem;
+    rem /= g->by;
+    g->bz = D < rem ? D : rem;
+    rem /= g->bz;
+    g->bb = rem;
+    if ((long long)g->bx * g->by * g->bz * g->bb != rows || g->bb > B || B % g->bb) return false;
+    g->nx = W / g->bx;
+    g->ny = H / g->by;
+    g->nz = D / g->bz;
+    return true;
 }
 
-// Tensor map over a channels-last BF16 tensor of C channels whose voxel grid is
-// (B, D, H, W) with voxel strides (sx, sy, sz, sb) in elements, box (8, box).
-int encode(CUtensorMap* m, const void* base, int C, int B, int D, int H, int W, long long sx, long long sy,
-           long long sz, long long sb, const Box& box) {
+long long n_tiles(const TileGrid& g) { return (long long)g.nx * g.ny * g.nz * (g.B / g.bb); }
+long long n_voxels(const TileGrid& g) { return (long long)g.B * g.D * g.H * g.W; }
+
+int encode(CUtensorMap* m, const void* base, const cuuint64_t dims[5], const cuuint64_t strides[4],
+           const cuuint32_t box[5]) {
     auto fn = encode_fn();
     if (!fn) return fail(SPNN_ECUDA, "cuTensorMapEncodeTiled unavailable");
     if (reinterpret_cast<uintptr_t>(base) % 16) return fail(SPNN_EINVAL, "tensor base not 16-byte aligned");
-    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
-    cuuint64_t strides[4] = {(cuuint64_t)(sx * 2), (cuuint64_t)(sy * 2), (cuuint64_t)(sz * 2),
-                             (cuuint64_t)(sb * 2)};
-    cuuint32_t bdim[5] = {8, (cuuint32_t)box.x, (cuuint32_t)box.y, (cuuint32_t)box.z, (cuuint32_t)box.b};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, bdim, estr,
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SPNN_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return SPNN_OK;
 }
 
-// Plain map over a (B, D, H, W, C) tensor.
-int map_plain(CUtensorMap* m, const void* p, int C, int B, int D, int H, int W, const Box& box) {
-    const long long sx = C, sy = (long long)W * C, sz = sy * H, sb = sz * D;
-    return encode(m, p, C, B, D, H, W, sx, sy, sz, sb, box);
+// Chunk-plane tensor [C/8][B][D][H][W][8] on grid g: dims (8W, H, D, B, C/8);
+// coordinates (8x, y, z, b, c8).  Default box (8 bx, by, bz, bb, planes); the
+// conv3 halo box is (8 bx, by + 2, 3, 1, planes).
+int map_planes(CUtensorMap* m, const void* p, int C, const TileGrid& g, int planes = 1, bool halo = false) {
+    const cuuint64_t row = 16ull * g.W;
+    cuuint64_t dims[5] = {8ull * g.W, (cuuint64_t)g.H, (cuuint64_t)g.D, (cuuint64_t)g.B, (cuuint64_t)(C / 8)};
+    cuuint64_t strides[4] = {row, row * g.H, row * g.H * g.D, row * g.H * g.D * g.B};
+    cuuint32_t box[5] = {8u * g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz, (cuuint32_t)g.bb, (cuuint32_t)planes};
+    if (halo) {
+        box[1] = g.by + 2;
+        box[2] = 3;
+        box[3] = 1;
+    }
+    return encode(m, p, dims, strides, box);
 }
 
-// Stride-2 view of a fine (B, 2D, 2H, 2W, C) tensor at offset o = (oz, oy, ox),
-// indexed by the coarse grid (B, D, H, W).
-int map_strided(CUtensorMap* m, const void* p, int C, int B, int D, int H, int W, int o, const Box& box) {
-    const int Wf = 2 * W, Hf = 2 * H, Df = 2 * D;
+// Stride-2 view at offset o = (oz, oy, ox) of a fine chunk-plane tensor of grid
+// (B, 2D, 2H, 2W), indexed by the coarse grid g: dims (8, W, H, D, C/8 * B),
+// box (8, bx, by, bz, bb); coordinates (0, x, y, z, c8 B + b).
+int map_strided(CUtensorMap* m, const void* p, int C, const TileGrid& g, int o) {
+    const long long Wf = 2LL * g.W, Hf = 2LL * g.H, Df = 2LL * g.D;
     const int oz = o >> 2, oy = (o >> 1) & 1, ox = o & 1;
-    const __nv_bfloat16* base =
-        static_cast<const __nv_bfloat16*>(p) + (((long long)oz * Hf + oy) * Wf + ox) * C;
-    const long long sx = 2LL * C, sy = 2LL * Wf * C, sz = 2LL * Hf * Wf * C, sb = (long long)Df * Hf * Wf * C;
-    return encode(m, base, C, B, D, H, W, sx, sy, sz, sb, box);
+    const __nv_bfloat16* base = static_cast<const __nv_bfloat16*>(p) + ((oz * Hf + oy) * Wf + ox) * 8;
+    cuuint64_t dims[5] = {8, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)g.D, (cuuint64_t)(C / 8) * g.B};
+    cuuint64_t strides[4] = {32, (cuuint64_t)(32 * Wf), (cuuint64_t)(32 * Wf * Hf), (cuuint64_t)(16 * Wf * Hf * Df)};
+    cuuint32_t box[5] = {8, (cuuint32_t)g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz, (cuuint32_t)g.bb};
+    return encode(m, base, dims, strides, box);
 }
 
 int n_taps_of(int kind) { return kind == KIND_CONV3 ? 27 : 8; }
 
 
 // ------------------------------------------------------------ rows GEMM --
-int rows_gemm(RowsParams& p, long long rows, cudaStream_t st) {
-    if (p.n_total <= 0 || p.n_total % 16) return fail(SPNN_EINVAL, "GEMM N %d not a multiple of 16", p.n_total);
+// Choose the K-step geometry of a rows GEMM (maps already hold their boxes).
+void rows_geometry(RowsParams& p) {
     p.n_tile = p.n_total <= 256 ? p.n_total : 256;
-    if (p.n_total % p.n_tile) return fail(SPNN_EINVAL, "GEMM N %d > 256 not a multiple of 256", p.n_total);
-    if (p.kc_total < 2 || p.kc_total % 2) return fail(SPNN_EINVAL, "input channels not a multiple of 16");
-    int ks = p.kc_total < 8 ? p.kc_total : 8;
-    while (p.kc_total % ks) ks -= 2;
-    p.kc_step = ks;
-    p.ksteps = p.n_taps * (p.kc_total / ks);
-    p.a_stage_bytes = 2048u * ks;
-    p.b_stage_bytes = (uint32_t)(ks * p.n_tile * 16);
+    if (p.tap_mode == TAP_SHIFT3) {
+        const uint32_t nrow = (uint32_t)p.n_tile * 16u;
+        p.halo_plane = (uint32_t)(p.g.bx * (p.g.by + 2) * 3 * 16);
+        p.a_stage_bytes = p.halo ? p.E * p.halo_plane : 9u * p.E * 2048u;
+        p.b_stage_bytes = 9u * p.E * nrow;
+        p.ksteps = 3 * (p.kc_total / p.E);
+    } else {
+        p.ksteps = p.n_taps * (p.kc_total / p.kc_step);
+        p.a_stage_bytes = 2048u * p.kc_step;
+        p.b_stage_bytes = (uint32_t)(p.kc_step * p.n_tile * 16);
+    }
     p.stage_bytes = (p.a_stage_bytes + p.b_stage_bytes + 1023u) & ~1023u;
-    int S = (int)((100u * 1024u) / p.stage_bytes);
+}
+
+// Planes per conv3 K-step: 4 when both concatenated sources divide by 4 and
+// the stage (A boxes + nine taps of B) stays within 56 KB, else 2.
+int conv_planes(int kc0, int kc1, const TileGrid& g, int n_total, bool halo) {
+    if (kc0 % 4 || kc1 % 4) return 2;
+    const long long n_tile = n_total <= 256 ? n_total : 256;
+    const long long a = halo ? 4LL * g.bx * (g.by + 2) * 3 * 16 : 9LL * 4 * 2048;
+    const long long b = 9LL * 4 * n_tile * 16;
+    return a + b <= 56 * 1024 ? 4 : 2;
+}
+
+// Chunk planes per K-step for the other modes: the largest even divisor of kc_total up to 8.
+int plain_kc_step(int kc_total) {
+    int ks = kc_total < 8 ? kc_total : 8;
+    while (kc_total % ks) ks -= 2;
+    return ks;
+}
+
+int rows_gemm(RowsParams& p, cudaStream_t st) {
+    if (p.n_total <= 0 || p.n_total % 16) return fail(SPNN_EINVAL, "GEMM N %d not a multiple of 16", p.n_total);
+    if (p.n_total > 256 && p.n_total % 256) return fail(SPNN_EINVAL, "GEMM N %d > 256 not a multiple of 256", p.n_total);
+    if (p.kc_total < 2 || p.kc_total % 2) return fail(SPNN_EINVAL, "input channels not a multiple of 16");
+    rows_geometry(p);
+    int S = (int)((110u * 1024u) / p.stage_bytes);
     p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
-    // K-major no-swizzle operands: the leading-dimension offset is the step
-    // between 16-byte chunk planes along K (2048 for A, n_tile*16 for B), the
-    // stride-dimension offset the step between 8-row groups (128).
+    // K-major no-swizzle operands: leading-dimension offset = step between
+    // 16-byte chunk planes along K, stride-dimension offset = step between
+    // 8-row groups (128 bytes); the kernel builds the descriptors.
     p.idesc = idesc_bf16(128, p.n_tile, 0, 0);
-    p.lbo_a = 2048;
-    p.sbo_a = 128;
-    p.lbo_b = (uint32_t)(p.n_tile * 16);
-    p.sbo_b = 128;
     p.err = err_ptr();
     if (!p.err) return fail(SPNN_ECUDA, "no device");
     size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
-    if (rows % kRows) return fail(SPNN_EINVAL, "rows %lld not a multiple of 128", rows);
-    cudaError_t e = launch_rows(p, (int)(rows / kRows), p.n_total / p.n_tile, smem, st);
+    if (smem > 227 * 1024) return fail(SPNN_EINVAL, "stage of %u bytes does not fit", p.stage_bytes);
+    cudaError_t e = launch_rows(p, (int)n_tiles(p.g), p.n_total / p.n_tile, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "rows_kernel launch");
     return SPNN_OK;
 }
@@ -161,9 +193,7 @@ int rows_gemm(RowsParams& p, long long rows, cudaStream_t st) {
 // ----------------------------------------------------------- wgrad GEMM --
 int wgrad_gemm(WgradParams& p, int btaps, cudaStream_t st) {
     if (p.n <= 0 || p.n % 16 || p.n > 256) return fail(SPNN_EINVAL, "wgrad N %d must be 16..256, step 16", p.n);
-    const long long vox = (long long)p.V_B * p.V_D * p.V_H * p.V_W;
-    if (vox % kWgradK) return fail(SPNN_EINVAL, "wgrad voxels not a multiple of 64");
-    p.ksteps_total = (int)(vox / kWgradK);
+    p.ksteps_total = (int)n_tiles(p.g);
     const int groups_all = p.n_groups + (p.ones_group >= 0 ? 1 : 0);
     const int m_tiles = (groups_all + 15) / 16;
     int splits = (4 * 152 + m_tiles * btaps - 1) / (m_tiles * btaps);
@@ -171,17 +201,17 @@ int wgrad_gemm(WgradParams& p, int btaps, cudaStream_t st) {
     if (splits > p.ksteps_total) splits = p.ksteps_total;
     p.ksteps_per_cta = (p.ksteps_total + splits - 1) / splits;
     splits = (p.ksteps_total + p.ksteps_per_cta - 1) / p.ksteps_per_cta;
-    p.a_stage_bytes = 16u * 1024u;
-    p.b_stage_bytes = (uint32_t)(p.n * 128);
+    const uint32_t gbytes = (uint32_t)p.kv * 16u;
+    p.a_stage_bytes = 16u * gbytes;
+    p.b_stage_bytes = (uint32_t)(p.n / 8) * gbytes;
     p.stage_bytes = p.a_stage_bytes + p.b_stage_bytes;
     int S = (int)((100u * 1024u) / p.stage_bytes);
     p.stages = S < 2 ? 2 : (S > 6 ? 6 : S);
-    // MN-major no-swizzle operands: leading-dimension offset = step between
-    // 8-voxel core matrices along K (128), stride-dimension offset = step
-    // between 8-channel groups along M / N (one 1 KB box, 1024).
+    // MN-major no-swizzle operands (descriptors built in the kernel):
+    // leading-dimension offset = step between 8-voxel core matrices along K
+    // (128 bytes), stride-dimension offset = step between 8-channel groups
+    // along M / N (one group block, kv * 16 bytes).
     p.idesc = idesc_bf16(128, p.n, 1, 1);
-    p.lbo = 128;
-    p.sbo = 1024;
     p.err = err_ptr();
     if (!p.err) return fail(SPNN_ECUDA, "no device");
     size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
@@ -195,9 +225,13 @@ int wgrad_gemm(WgradParams& p, int btaps, cudaStream_t st) {
 namespace {
 
 // ------------------------------------------------------------- packing --
-// Packed operand element (tile, tap, kc, nn, e) with dims (n_tiles, taps_p,
-// kc_total, n_tile, 8) holds B[n = tile * n_tile + nn][k = kc * 8 + e] of the
-// GEMM for that tap; the source is the FP32 master W[t][ci][co].
+// Packed operand B[n][k] of one GEMM, n = output column, k = (tap, input
+// channel), BF16, grouped in 16-byte chunks of 8 consecutive k:
+//   conv3     [n tiles][dx + 1][kc][(dz + 1) * 3 + (dy + 1)][n_tile][8]
+//             (the nine taps of one x-shift and one 8-channel chunk kc are
+//             adjacent, so a K-step over (x-shift, chunk block) is one copy);
+//   down / up [n tiles][taps][kc][n_tile][8].
+// The source is the FP32 master W[t][ci][co], t = (dz+1)*9 + (dy+1)*3 + (dx+1).
 __global__ void pack_kernel(int kind, int which, int cin, int cout, int taps_p, int kc_total, int n_tile,
                             const float* __restrict__ w, __nv_bfloat16* __restrict__ out, long long total) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -207,10 +241,21 @@ __global__ void pack_kernel(int kind, int which, int cin, int cout, int taps_p, 
         r /= 8;
         const int nn = (int)(r % n_tile);
         r /= n_tile;
-        const int kc = (int)(r % kc_total);
-        r /= kc_total;
-        const int tap = (int)(r % taps_p);
-        const int tile = (int)(r / taps_p);
+        int tap, kc, tile;
+        if (kind == KIND_CONV3) {
+            const int t9 = (int)(r % 9);
+            r /= 9;
+            kc = (int)(r % kc_total);
+            r /= kc_total;
+            const int dxi = (int)(r % 3);
+            tile = (int)(r / 3);
+            tap = t9 * 3 + dxi;      // (dz+1)*9 + (dy+1)*3 + (dx+1)
+        } else {
+            kc = (int)(r % kc_total);
+            r /= kc_total;
+            tap = (int)(r % taps_p);
+            tile = (int)(r / taps_p);
+        }
         const int n = tile * n_tile + nn, k = kc * 8 + e;
         int t, ci, co;
         if (which == SPNN_PACK_FWD) {
@@ -268,16 +313,21 @@ int grid_ok(int B, int D, int H, int W) {
     return SPNN_OK;
 }
 
-EpiDest dest(void* out, int ld, int col0, const void* addend, const void* mask, const float* bias, int relu) {
+EpiDest dest(void* out, long long plane, int col0, const void* addend, const void* mask, const float* bias,
+             int relu) {
     EpiDest d;
     d.out = static_cast<__nv_bfloat16*>(out);
     d.addend = static_cast<const __nv_bfloat16*>(addend);
     d.mask = static_cast<const __nv_bfloat16*>(mask);
     d.bias = bias;
-    d.ld = ld;
+    d.plane = plane;
     d.col0 = col0;
     d.relu = relu;
     return d;
+}
+
+int bad_grid(int rows, const TileGrid&) {
+    return fail(SPNN_EINVAL, "grid does not tile into %d-voxel boxes", rows);
 }
 
 int layer_forward(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
@@ -293,47 +343,41 @@ int layer_forward(int kind, int B, int D, int H, int W, const void* x0, int c0, 
         return fail(SPNN_EINVAL, "fused head needs conv3, cout <= 256, head_w and head_b");
     RowsParams p;
     memset(&p, 0, sizeof p);
-    int RD = D, RH = H, RW = W;
-    if (kind == KIND_DOWN) {
-        RD /= 2;
-        RH /= 2;
-        RW /= 2;
-    }
-    Box box;
-    if (!make_box(kRows, B, RD, RH, RW, &box))
-        return fail(SPNN_EINVAL, "row grid (%d, %d, %d, %d) does not tile into 128-voxel boxes", B, RD, RH, RW);
+    const int s = kind == KIND_DOWN ? 2 : 1;
+    if (!make_grid(kRows, B, D / s, H / s, W / s, &p.g)) return bad_grid(kRows, p.g);
+    p.kc_total = (c0 + c1) / 8;
+    p.kc0 = c0 / 8;
     if (kind == KIND_CONV3) {
         p.tap_mode = TAP_SHIFT3;
         p.n_taps = 27;
-        if ((rc = map_plain(&p.maps[0], x0, c0, B, D, H, W, box))) return rc;
-        if (c1 && (rc = map_plain(&p.maps[1], x1, c1, B, D, H, W, box))) return rc;
+        p.halo = p.g.bz == 1 && p.g.bb == 1;
+        p.E = conv_planes(c0 / 8, c1 / 8, p.g, cout, p.halo);
+        if ((rc = map_planes(&p.maps[0], x0, c0, p.g, p.E, p.halo))) return rc;
+        if (c1 && (rc = map_planes(&p.maps[1], x1, c1, p.g, p.E, p.halo))) return rc;
     } else if (kind == KIND_DOWN) {
         p.tap_mode = TAP_MAP;
         p.n_taps = 8;
+        p.kc_step = plain_kc_step(p.kc_total);
         for (int o = 0; o < 8; ++o)
-            if ((rc = map_strided(&p.maps[o], x0, c0, B, RD, RH, RW, o, box))) return rc;
+            if ((rc = map_strided(&p.maps[o], x0, c0, p.g, o))) return rc;
     } else {
         p.tap_mode = TAP_NONE;
         p.n_taps = 1;
-        if ((rc = map_plain(&p.maps[0], x0, c0, B, D, H, W, box))) return rc;
+        p.kc_step = plain_kc_step(p.kc_total);
+        if ((rc = map_planes(&p.maps[0], x0, c0, p.g, p.kc_step))) return rc;
     }
-    p.kc_total = (c0 + c1) / 8;
-    p.kc0 = c0 / 8;
     p.wpack = static_cast<const __nv_bfloat16*>(packed);
-    p.R_B = B;
-    p.R_D = RD;
-    p.R_H = RH;
-    p.R_W = RW;
     p.n_total = kind == KIND_UP ? 8 * cout : cout;
     p.scatter_up = kind == KIND_UP;
     p.cout_up = cout;
     p.split = p.n_total;
-    p.d[0] = dest(y, cout, 0, nullptr, nullptr, bias, relu);
+    const long long out_vox = n_voxels(p.g) * (kind == KIND_UP ? 8 : 1);
+    p.d[0] = dest(y, out_vox * 8, 0, nullptr, nullptr, bias, relu);
     p.d[1] = p.d[0];
     p.head_out = head_out;
     p.head_w = head_w;
     p.head_b = head_b;
-    return rows_gemm(p, (long long)B * RD * RH * RW, st);
+    return rows_gemm(p, st);
 }
 
 int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, const void* packed, int c0,
@@ -343,48 +387,49 @@ int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, 
     if ((rc = check_kind(kind, c0 + c1, cout)) || (rc = grid_ok(B, D, H, W))) return rc;
     if (!dy || !packed || !dx0 || (c1 && !dx1)) return fail(SPNN_EINVAL, "null tensor");
     if (c1 && kind != KIND_CONV3) return fail(SPNN_EINVAL, "split input gradient only for conv3");
+    if (c0 % 16 || c1 % 16) return fail(SPNN_EINVAL, "input-gradient destinations need multiples of 16 channels");
     RowsParams p;
     memset(&p, 0, sizeof p);
-    Box box;
+    const long long in_vox = (long long)B * D * H * W;
+    p.kc_total = cout / 8;
+    p.kc0 = p.kc_total;
     if (kind == KIND_CONV3) {
-        if (!make_box(kRows, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 128 rows");
-        if ((rc = map_plain(&p.maps[0], dy, cout, B, D, H, W, box))) return rc;
+        if (!make_grid(kRows, B, D, H, W, &p.g)) return bad_grid(kRows, p.g);
+        p.halo = p.g.bz == 1 && p.g.bb == 1;
+        p.E = conv_planes(p.kc_total, 0, p.g, c0 + c1, p.halo);
+        if ((rc = map_planes(&p.maps[0], dy, cout, p.g, p.E, p.halo))) return rc;
         p.tap_mode = TAP_SHIFT3;
         p.n_taps = 27;
-        p.R_B = B, p.R_D = D, p.R_H = H, p.R_W = W;
         p.n_total = c0 + c1;
         p.split = c0;
-        p.d[0] = dest(dx0, c0, 0, add0, mask0, nullptr, 0);
-        p.d[1] = c1 ? dest(dx1, c1, c0, add1, mask1, nullptr, 0) : p.d[0];
+        p.d[0] = dest(dx0, in_vox * 8, 0, add0, mask0, nullptr, 0);
+        p.d[1] = c1 ? dest(dx1, in_vox * 8, c0, add1, mask1, nullptr, 0) : p.d[0];
     } else if (kind == KIND_DOWN) {
-        const int RD = D / 2, RH = H / 2, RW = W / 2;
-        if (!make_box(kRows, B, RD, RH, RW, &box)) return fail(SPNN_EINVAL, "grid does not tile into 128 rows");
-        if ((rc = map_plain(&p.maps[0], dy, cout, B, RD, RH, RW, box))) return rc;
+        if (!make_grid(kRows, B, D / 2, H / 2, W / 2, &p.g)) return bad_grid(kRows, p.g);
+        p.kc_step = plain_kc_step(p.kc_total);
+        if ((rc = map_planes(&p.maps[0], dy, cout, p.g, p.kc_step))) return rc;
         p.tap_mode = TAP_NONE;
         p.n_taps = 1;
-        p.R_B = B, p.R_D = RD, p.R_H = RH, p.R_W = RW;
         p.n_total = 8 * c0;
         p.split = p.n_total;
         p.scatter_up = 1;
         p.cout_up = c0;
-        p.d[0] = dest(dx0, c0, 0, add0, mask0, nullptr, 0);
+        p.d[0] = dest(dx0, in_vox * 8, 0, add0, mask0, nullptr, 0);
         p.d[1] = p.d[0];
     } else {
-        if (!make_box(kRows, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 128 rows");
+        if (!make_grid(kRows, B, D, H, W, &p.g)) return bad_grid(kRows, p.g);
+        p.kc_step = plain_kc_step(p.kc_total);
         for (int o = 0; o < 8; ++o)
-            if ((rc = map_strided(&p.maps[o], dy, cout, B, D, H, W, o, box))) return rc;
+            if ((rc = map_strided(&p.maps[o], dy, cout, p.g, o))) return rc;
         p.tap_mode = TAP_MAP;
         p.n_taps = 8;
-        p.R_B = B, p.R_D = D, p.R_H = H, p.R_W = W;
         p.n_total = c0;
         p.split = c0;
-        p.d[0] = dest(dx0, c0, 0, add0, mask0, nullptr, 0);
+        p.d[0] = dest(dx0, in_vox * 8, 0, add0, mask0, nullptr, 0);
         p.d[1] = p.d[0];
     }
-    p.kc_total = cout / 8;
-    p.kc0 = p.kc_total;
     p.wpack = static_cast<const __nv_bfloat16*>(packed);
-    return rows_gemm(p, (long long)p.R_B * p.R_D * p.R_H * p.R_W, st);
+    return rows_gemm(p, st);
 }
 
 int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
@@ -402,29 +447,39 @@ int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, co
     p.n = cout;
     p.dw = dw;
     p.db = db;
-    Box box;
     int btaps = 1;
+    const int s = kind == KIND_DOWN ? 2 : 1;
+    // 128-voxel K-steps while the stage stays small, else 64
+    p.kv = cout <= 64 ? 128 : 64;
+    if (!make_grid(p.kv, B, D / s, H / s, W / s, &p.g)) {
+        p.kv = 64;
+        if (!make_grid(p.kv, B, D / s, H / s, W / s, &p.g)) return bad_grid(p.kv, p.g);
+    }
+    // planes per box: runs of consecutive chunks of one tap and one source,
+    // aligned to the 16-group M tiles
+    auto run = [](int a, int b) {
+        int e = 16;
+        while (e > 1 && ((a % e) || (b % e))) e /= 2;
+        return e;
+    };
+    p.eb = kind == KIND_UP ? 1 : run(cout / 8, cout / 8);
     if (kind == KIND_CONV3) {
-        p.V_B = B, p.V_D = D, p.V_H = H, p.V_W = W;
-        if (!make_box(kWgradK, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 64 voxels");
-        if ((rc = map_plain(&p.amaps[0], x0, c0, B, D, H, W, box))) return rc;
-        if (c1 && (rc = map_plain(&p.amaps[1], x1, c1, B, D, H, W, box))) return rc;
-        if ((rc = map_plain(&p.bmaps[0], dy, cout, B, D, H, W, box))) return rc;
+        p.ea = run(c0 / 8, c1 ? c1 / 8 : c0 / 8);
+        if ((rc = map_planes(&p.amaps[0], x0, c0, p.g, p.ea))) return rc;
+        if (c1 && (rc = map_planes(&p.amaps[1], x1, c1, p.g, p.ea))) return rc;
+        if ((rc = map_planes(&p.bmaps[0], dy, cout, p.g, p.eb))) return rc;
         p.n_groups = 27 * p.kc_total;
     } else if (kind == KIND_DOWN) {
-        const int RD = D / 2, RH = H / 2, RW = W / 2;
-        p.V_B = B, p.V_D = RD, p.V_H = RH, p.V_W = RW;
-        if (!make_box(kWgradK, B, RD, RH, RW, &box)) return fail(SPNN_EINVAL, "grid does not tile into 64 voxels");
+        p.ea = 1;
         for (int o = 0; o < 8; ++o)
-            if ((rc = map_strided(&p.amaps[o], x0, c0, B, RD, RH, RW, o, box))) return rc;
-        if ((rc = map_plain(&p.bmaps[0], dy, cout, B, RD, RH, RW, box))) return rc;
+            if ((rc = map_strided(&p.amaps[o], x0, c0, p.g, o))) return rc;
+        if ((rc = map_planes(&p.bmaps[0], dy, cout, p.g, p.eb))) return rc;
         p.n_groups = 8 * p.kc_total;
     } else {
-        p.V_B = B, p.V_D = D, p.V_H = H, p.V_W = W;
-        if (!make_box(kWgradK, B, D, H, W, &box)) return fail(SPNN_EINVAL, "grid does not tile into 64 voxels");
-        if ((rc = map_plain(&p.amaps[0], x0, c0, B, D, H, W, box))) return rc;
+        p.ea = run(c0 / 8, c0 / 8);
+        if ((rc = map_planes(&p.amaps[0], x0, c0, p.g, p.ea))) return rc;
         for (int o = 0; o < 8; ++o)
-            if ((rc = map_strided(&p.bmaps[o], dy, cout, B, D, H, W, o, box))) return rc;
+            if ((rc = map_strided(&p.bmaps[o], dy, cout, p.g, o))) return rc;
         p.n_groups = p.kc_total;
         btaps = 8;
     }
@@ -435,6 +490,7 @@ int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, co
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 // --------------------------------------------------------- data kernels --
+// Input features in chunk planes: plane 0 holds channels 0-7, plane 1 channels 8-15 (zero).
 __global__ void pack_input_kernel(const uint8_t* __restrict__ mask, const float* __restrict__ optics, int D,
                                   long long vox_per_sample, long long total, __nv_bfloat16* __restrict__ x,
                                   int HW) {
@@ -444,14 +500,13 @@ __global__ void pack_input_kernel(const uint8_t* __restrict__ mask, const float*
         const int z = (int)((i % vox_per_sample) / HW);
         const float pore = mask[i] ? 1.f : 0.f;
         const float mus = optics[3 * b], mua = optics[3 * b + 1], g = optics[3 * b + 2];
-        float f[16] = {pore, 1.f - pore, logf(mus), 0.25f * logf(mua), g, (z + 0.5f) / (float)D};
-        uint4 w[2];
-        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
+        const float f[8] = {pore, 1.f - pore, logf(mus), 0.25f * logf(mua), g, (z + 0.5f) / (float)D, 0.f, 0.f};
+        uint4 w;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&w);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
-        uint4* dst = reinterpret_cast<uint4*>(x + i * 16);
-        dst[0] = w[0];
-        dst[1] = w[1];
+        for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+        *reinterpret_cast<uint4*>(x + i * 8) = w;
+        *reinterpret_cast<uint4*>(x + (total + i) * 8) = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -528,7 +583,8 @@ __global__ void loss_head_kernel(const float* __restrict__ pred, const float* __
         acc[C] += dp;
 #pragma unroll
         for (int c0 = 0; c0 < C; c0 += 8) {
-            const uint4 u = *reinterpret_cast<const uint4*>(act + i * C + c0);
+            const long long off = (c0 / 8) * total * 8 + i * 8;   // chunk plane c0 / 8, voxel i
+            const uint4 u = *reinterpret_cast<const uint4*>(act + off);
             const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
             uint4 o;
             __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
@@ -540,7 +596,7 @@ __global__ void loss_head_kernel(const float* __restrict__ pred, const float* __
                 acc[c + 1] += dp * a.y;
                 oh[k] = __floats2bfloat162_rn(a.x > 0.f ? dp * hw[c] : 0.f, a.y > 0.f ? dp * hw[c + 1] : 0.f);
             }
-            *reinterpret_cast<uint4*>(g + i * C + c0) = o;
+            *reinterpret_cast<uint4*>(g + off) = o;
         }
     }
 #pragma unroll

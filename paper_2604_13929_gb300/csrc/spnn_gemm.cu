@@ -18,9 +18,9 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-__device__ __forceinline__ void load16_bf16(const __nv_bfloat16* p, float (&f)[16]) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    uint4 u[2] = {q[0], q[1]};
+// 16 channels of one voxel: 8 at p[0..7] and 8 one chunk plane further.
+__device__ __forceinline__ void load16_planes(const __nv_bfloat16* p, long long plane, float (&f)[16]) {
+    uint4 u[2] = {*reinterpret_cast<const uint4*>(p), *reinterpret_cast<const uint4*>(p + plane)};
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(u);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -28,6 +28,15 @@ __device__ __forceinline__ void load16_bf16(const __nv_bfloat16* p, float (&f)[1
         f[2 * i] = t.x;
         f[2 * i + 1] = t.y;
     }
+}
+
+// TMA box of chunk plane c8: chunk-plane map (8x, y, z, b, c8) or stride-2 view (0, x, y, z, c8 B + b).
+__device__ __forceinline__ void load_box(uint32_t dst, const CUtensorMap* m, uint32_t bar, bool strided, int c8,
+                                         int x, int y, int z, int b, int B) {
+    if (strided)
+        tma_load_5d(dst, m, bar, 0, x, y, z, c8 * B + b);
+    else
+        tma_load_5d(dst, m, bar, 8 * x, y, z, b, c8);
 }
 
 // ------------------------------------------------------------------------
@@ -64,17 +73,13 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const long long row0 = (long long)blockIdx.x * kRows;
-    const int x0 = (int)(row0 % p.R_W);
-    long long t = row0 / p.R_W;
-    const int y0 = (int)(t % p.R_H);
-    t /= p.R_H;
-    const int z0 = (int)(t % p.R_D);
-    const int b0 = (int)(t / p.R_D);
+    int x0, y0, z0, b0;
+    tile_origin(p.g, blockIdx.x, x0, y0, z0, b0);
 
+    const bool conv = p.tap_mode == TAP_SHIFT3;
     if (warp == 0) {
         if (lane == 0) {
-            const int gpt = p.kc_total / p.kc_step;
+            const int gpt = conv ? p.kc_total / p.E : p.kc_total / p.kc_step;
             const uint32_t tx = p.a_stage_bytes + p.b_stage_bytes;
             for (int k = 0; k < p.ksteps; ++k) {
                 const int s = k % S;
@@ -85,37 +90,41 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                     break;
                 }
                 mbar_expect_tx(full, tx);
-                const int tap = k / gpt, g = k % gpt;
-                int dx = 0, dy = 0, dz = 0;
-                if (p.tap_mode == TAP_SHIFT3) {
-                    dz = tap / 9 - 1;
-                    dy = (tap / 3) % 3 - 1;
-                    dx = tap % 3 - 1;
-                }
                 const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-                for (int j = 0; j < p.kc_step; ++j) {
-                    const int kc = g * p.kc_step + j;
-                    int mi, c;
-                    if (p.tap_mode == TAP_MAP) {
-                        mi = tap;
-                        c = kc * 8;
-                    } else if (kc < p.kc0) {
-                        mi = 0;
-                        c = kc * 8;
+                const int tap = k / gpt, g = k % gpt;
+                if (conv) {
+                    // tap = x-shift index, g = block of E chunk planes
+                    const int dx = tap - 1, kc = g * p.E;
+                    const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
+                    if (p.halo) {
+                        tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 + dx), y0 - 1, z0 - 1, b0, c8);
                     } else {
-                        mi = 1;
-                        c = (kc - p.kc0) * 8;
+                        for (int t9 = 0; t9 < 9; ++t9)
+                            tma_load_5d(a_dst + (uint32_t)(t9 * p.E) * 2048u, &p.maps[mi], full, 8 * (x0 + dx),
+                                        y0 + (t9 % 3) - 1, z0 + (t9 / 3) - 1, b0, c8);
                     }
-                    tma_load_5d(a_dst + 2048u * j, &p.maps[mi], full, c, x0 + dx, y0 + dy, z0 + dz, b0);
+                    const __nv_bfloat16* src =
+                        p.wpack + ((size_t)(blockIdx.y * 3 + tap) * p.kc_total + kc) * 9 * p.n_tile * 8;
+                    bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
+                } else {
+                    if (p.tap_mode == TAP_MAP) {
+                        for (int j = 0; j < p.kc_step; ++j)
+                            load_box(a_dst + 2048u * j, &p.maps[tap], full, true, g * p.kc_step + j, x0, y0, z0,
+                                     b0, p.g.B);
+                    } else {
+                        // TAP_NONE: one box of kc_step chunk planes
+                        tma_load_5d(a_dst, &p.maps[0], full, 8 * x0, y0, z0, b0, g * p.kc_step);
+                    }
+                    const __nv_bfloat16* src =
+                        p.wpack + ((size_t)(blockIdx.y * p.n_taps + tap) * p.kc_total + (size_t)g * p.kc_step) *
+                                      p.n_tile * 8;
+                    bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
                 }
-                const __nv_bfloat16* src =
-                    p.wpack + ((size_t)(blockIdx.y * p.n_taps + tap) * p.kc_total + (size_t)g * p.kc_step) *
-                                  p.n_tile * 8;
-                bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            const uint32_t nrow = (uint32_t)p.n_tile * 16u;   // bytes of one packed chunk of B
             for (int k = 0; k < p.ksteps; ++k) {
                 const int s = k % S;
                 const uint32_t r = (uint32_t)(k / S);
@@ -126,10 +135,25 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 tc_fence_after();
                 const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
                 const uint32_t b0s = a0 + p.a_stage_bytes;
-                for (int i = 0; i < p.kc_step / 2; ++i) {
-                    const uint64_t ad = smem_desc(a0 + 4096u * i, p.lbo_a, p.sbo_a);
-                    const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * p.n_tile * 16), p.lbo_b, p.sbo_b);
-                    umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                if (conv) {
+                    const uint32_t rowb = (uint32_t)p.g.bx * 16u;
+                    for (int t9 = 0; t9 < 9; ++t9) {
+                        const uint32_t a_tap =
+                            p.halo ? a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb
+                                   : a0 + (uint32_t)(t9 * p.E) * 2048u;
+                        const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
+                        for (int i = 0; i < p.E / 2; ++i) {
+                            const uint64_t ad = smem_desc(a_tap + 2u * i * lbo_a, lbo_a, 128);
+                            const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
+                            umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                        }
+                    }
+                } else {
+                    for (int i = 0; i < p.kc_step / 2; ++i) {
+                        const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
+                        const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
+                        umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                    }
                 }
                 umma_commit(bar0 + 8u * (S + s));
             }
@@ -138,20 +162,14 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
     } else {
         const int q = warp & 3;
         const int r = q * 32 + lane;
-        const long long grow = row0 + r;
         bool ok = mbar_wait(done, 0, kWaitLimitNs);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) {
             if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
         } else {
             tc_fence_after();
-            // coarse-grid coordinates of this row (for the 2x upsampling scatter)
-            const int vx = (int)(grow % p.R_W);
-            long long tt = grow / p.R_W;
-            const int vy = (int)(tt % p.R_H);
-            tt /= p.R_H;
-            const int vz = (int)(tt % p.R_D);
-            const long long vb = tt / p.R_D;
+            int vx, vy, vz, vb;
+            const long long vox = row_voxel(p.g, x0, y0, z0, b0, r, &vx, &vy, &vz, &vb);
             float head_acc = 0.f;
             for (int j = 0; j < p.n_tile / 16; ++j) {
                 uint32_t v[16];
@@ -166,13 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                     const int o = n0 / p.cout_up;
                     ch0 = n0 % p.cout_up;
                     const int oz = o >> 2, oy = (o >> 1) & 1, ox = o & 1;
-                    const long long fine =
-                        ((vb * (2LL * p.R_D) + 2 * vz + oz) * (2LL * p.R_H) + 2 * vy + oy) * (2LL * p.R_W) +
-                        2 * vx + ox;
-                    off = fine * d.ld + ch0;
+                    const long long fine = (((long long)vb * (2 * p.g.D) + 2 * vz + oz) * (2 * p.g.H) + 2 * vy + oy) *
+                                               (2LL * p.g.W) +
+                                           2 * vx + ox;
+                    off = (ch0 >> 3) * d.plane + fine * 8;
                 } else {
                     ch0 = n0 - d.col0;
-                    off = grow * d.ld + ch0;
+                    off = (ch0 >> 3) * d.plane + vox * 8;
                 }
                 float f[16];
 #pragma unroll
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 }
                 if (d.addend) {
                     float a[16];
-                    load16_bf16(d.addend + off, a);
+                    load16_planes(d.addend + off, d.plane, a);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) f[i] += a[i];
                 }
@@ -193,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 }
                 if (d.mask) {
                     float m[16];
-                    load16_bf16(d.mask + off, m);
+                    load16_planes(d.mask + off, d.plane, m);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) f[i] = (m[i] > 0.f) ? f[i] : 0.f;
                 }
@@ -201,9 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-                uint4* dst = reinterpret_cast<uint4*>(d.out + off);
-                dst[0] = w[0];
-                dst[1] = w[1];
+                *reinterpret_cast<uint4*>(d.out + off) = w[0];
+                *reinterpret_cast<uint4*>(d.out + off + d.plane) = w[1];
                 if (p.head_out) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -212,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                     }
                 }
             }
-            if (p.head_out) p.head_out[grow] = head_acc + *p.head_b;
+            if (p.head_out) p.head_out[vox] = head_acc + *p.head_b;
         }
     }
     tc_fence_before();
@@ -249,12 +266,13 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     const int kbeg = blockIdx.x * p.ksteps_per_cta;
     const int kend = min(kbeg + p.ksteps_per_cta, p.ksteps_total);
 
+    const uint32_t gbytes = (uint32_t)p.kv * 16u;   // one group's block of a stage
     // bias group: bf16 ones in its slot of every stage (written once, never loaded over)
     const int ones_slot = (p.ones_group >= g0 && p.ones_group < g0 + 16) ? p.ones_group - g0 : -1;
     if (ones_slot >= 0) {
         for (int s = 0; s < S; ++s) {
-            uint32_t* dst = reinterpret_cast<uint32_t*>(smem + (size_t)s * p.stage_bytes + 1024 * ones_slot);
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) dst[i] = 0x3F803F80u;
+            uint32_t* dst = reinterpret_cast<uint32_t*>(smem + (size_t)s * p.stage_bytes + gbytes * ones_slot);
+            for (int i = threadIdx.x; i < (int)(gbytes / 4); i += blockDim.x) dst[i] = 0x3F803F80u;
         }
         fence_async_shared();
     }
@@ -279,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
         if (lane == 0) {
             int real = 0;
             for (int sl = 0; sl < ng; ++sl) real += (sl != ones_slot);
-            const uint32_t tx = 1024u * real + 128u * p.n;
+            const uint32_t tx = gbytes * real + (uint32_t)(p.n / 8) * gbytes;
             for (int k = kbeg; k < kend; ++k) {
                 const int kk = k - kbeg;
                 const int s = kk % S;
@@ -290,16 +308,14 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
                     break;
                 }
                 mbar_expect_tx(full, tx);
-                const long long v0 = (long long)k * kWgradK;
-                const int x0 = (int)(v0 % p.V_W);
-                long long t = v0 / p.V_W;
-                const int y0 = (int)(t % p.V_H);
-                t /= p.V_H;
-                const int z0 = (int)(t % p.V_D);
-                const int b0 = (int)(t / p.V_D);
+                int x0, y0, z0, b0;
+                tile_origin(p.g, k, x0, y0, z0, b0);
                 const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-                for (int sl = 0; sl < ng; ++sl) {
-                    if (sl == ones_slot) continue;
+                for (int sl = 0; sl < ng;) {
+                    if (sl == ones_slot) {
+                        ++sl;
+                        continue;
+                    }
                     const int g = g0 + sl;
                     int mi = 0, c8, dx = 0, dy = 0, dz = 0;
                     if (p.mode == KIND_CONV3) {
@@ -318,11 +334,15 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
                     } else {
                         c8 = g;
                     }
-                    tma_load_5d(a_dst + 1024u * sl, &p.amaps[mi], full, c8 * 8, x0 + dx, y0 + dy, z0 + dz, b0);
+                    // one box brings ea consecutive chunk planes (runs never straddle a tap or source)
+                    load_box(a_dst + gbytes * sl, &p.amaps[mi], full, p.mode == KIND_DOWN, c8, x0 + dx, y0 + dy,
+                             z0 + dz, b0, p.g.B);
+                    sl += p.ea;
                 }
                 const CUtensorMap* bm = &p.bmaps[p.mode == KIND_UP ? btap : 0];
-                for (int j = 0; j < p.n / 8; ++j)
-                    tma_load_5d(a_dst + p.a_stage_bytes + 1024u * j, bm, full, j * 8, x0, y0, z0, b0);
+                for (int j = 0; j < p.n / 8; j += p.eb)
+                    load_box(a_dst + p.a_stage_bytes + gbytes * j, bm, full, p.mode == KIND_UP, j, x0, y0, z0, b0,
+                             p.g.B);
             }
         }
     } else if (warp == 1) {
@@ -338,10 +358,9 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
                 tc_fence_after();
                 const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
                 const uint32_t b0s = a0 + p.a_stage_bytes;
-#pragma unroll
-                for (int i = 0; i < kWgradK / 16; ++i) {
-                    const uint64_t ad = smem_desc(a0 + 256u * i, p.lbo, p.sbo);
-                    const uint64_t bd = smem_desc(b0s + 256u * i, p.lbo, p.sbo);
+                for (int i = 0; i < p.kv / 16; ++i) {
+                    const uint64_t ad = smem_desc(a0 + 256u * i, 128u, gbytes);
+                    const uint64_t bd = smem_desc(b0s + 256u * i, 128u, gbytes);
                     umma_bf16(tmem, ad, bd, p.idesc, (kk > 0 || i > 0) ? 1u : 0u);
                 }
                 umma_commit(bar0 + 8u * (S + s));

@@ -1,5 +1,11 @@
 // spnn_internal.cuh -- launch parameter blocks shared by the surrogate's GEMM
 // kernels (spnn_gemm.cu) and its C ABI / runtime (spnn_api.cu).
+//
+// Activation layout ("chunk planes"): BF16 [C/8][B][D][H][W][8].  One plane
+// holds 8 channels of every voxel, 16 bytes per voxel, so a run of voxels
+// along x is contiguous and a TMA box row spans up to 32 voxels (512 bytes);
+// in shared memory a box lands as rows of 16 bytes, the no-swizzle core
+// matrix layout the tensor cores read.
 #pragma once
 
 #include <cuda.h>
@@ -19,30 +25,69 @@ enum { TAP_SHIFT3 = 0, TAP_MAP = 1, TAP_NONE = 2 };
 enum { ERR_TIMEOUT = 1 };
 
 constexpr int kRows = 128;                 // GEMM rows per CTA (MMA M)
-constexpr int kWgradK = 64;                // voxels per wgrad K-step
 constexpr int kThreads = 192;              // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
+// Tiles of a voxel grid: boxes of bx * by * bz * bb voxels (x fastest), nx *
+// ny * nz boxes per sample block; tile t -> box origin, row r -> voxel.
+struct TileGrid {
+    int B, D, H, W;
+    int bx, by, bz, bb;
+    int nx, ny, nz;
+};
+
+__host__ __device__ inline void tile_origin(const TileGrid& g, long long t, int& x0, int& y0, int& z0, int& b0) {
+    x0 = (int)(t % g.nx) * g.bx;
+    t /= g.nx;
+    y0 = (int)(t % g.ny) * g.by;
+    t /= g.ny;
+    z0 = (int)(t % g.nz) * g.bz;
+    b0 = (int)(t / g.nz) * g.bb;
+}
+
+// Linear voxel index ((b D + z) H + y) W + x of row r of the tile at (x0, y0, z0, b0).
+__host__ __device__ inline long long row_voxel(const TileGrid& g, int x0, int y0, int z0, int b0, int r,
+                                               int* vx, int* vy, int* vz, int* vb) {
+    const int x = x0 + r % g.bx;
+    r /= g.bx;
+    const int y = y0 + r % g.by;
+    r /= g.by;
+    const int z = z0 + r % g.bz;
+    const int b = b0 + r / g.bz;
+    *vx = x, *vy = y, *vz = z, *vb = b;
+    return (((long long)b * g.D + z) * g.H + y) * g.W + x;
+}
+
 struct EpiDest {
-    __nv_bfloat16* out;             // bf16 channels-last destination (may be null)
+    __nv_bfloat16* out;             // BF16 chunk-plane destination (may be null)
     const __nv_bfloat16* addend;    // added before the activation (same addressing), or null
     const __nv_bfloat16* mask;      // result zeroed where mask <= 0 (same addressing), or null
     const float* bias;              // per destination channel, or null
-    int ld;                         // channels of the destination tensor
+    long long plane;                // elements per chunk plane of the destination (voxels * 8)
     int col0;                       // first GEMM column that lands in this destination
     int relu;
 };
 
-// Rows GEMM: D[row, n] = sum_k A[row, k] B[n, k]; rows are 128 consecutive
-// voxels of the row grid, k = (tap, channel), A gathered by TMA boxes.
+// Rows GEMM: D[row, n] = sum_k A[row, k] B[n, k]; rows are the 128 voxels of
+// one box of the row grid, k = (tap, channel), A gathered by TMA boxes from
+// chunk-plane maps (coordinates 8x, y, z, b, c8) or, for TAP_MAP, stride-2
+// views (coordinates 0, x, y, z, c8 * B + b).
+//
+// conv3 (TAP_SHIFT3) K-steps are (x-shift dx, block of E chunk planes): with
+// `halo` set the tile is one z-plane and a single box of (bx, by + 2, 3)
+// voxels holds all nine (dz, dy) taps, each a descriptor offset into it;
+// otherwise nine boxes of the tile's own shape are loaded.  Other modes step
+// over (tap, kc_step chunk planes).
 struct RowsParams {
     CUtensorMap maps[8];
-    const __nv_bfloat16* wpack;     // [n tiles][taps][kc_total][n_tile][8]
+    const __nv_bfloat16* wpack;     // packed operand, layout per kind (see the packing kernel)
     int n_taps, kc_total, kc0, kc_step, tap_mode;
-    int R_B, R_D, R_H, R_W;
+    int halo, E;                    // conv3 only
+    uint32_t halo_plane;            // bytes of one chunk plane of the halo box
+    TileGrid g;
     int n_tile, n_total, ksteps, stages;
     uint32_t a_stage_bytes, b_stage_bytes, stage_bytes;
-    uint32_t idesc, lbo_a, sbo_a, lbo_b, sbo_b;
+    uint32_t idesc;
     int scatter_up, cout_up, split;
     EpiDest d[2];
     float* head_out;                // fused one-channel head: out = head_b + sum_c y_c head_w[c]
@@ -52,17 +97,21 @@ struct RowsParams {
 };
 
 // Weight-gradient GEMM: D[(group, r), n] = sum_v A_group[v, r] B[v, n] over a
-// range of 64-voxel K-steps; rows are 16 groups of 8 input channels (one tap
-// each), both operands MN-major, results added to fp32 dW with atomics.
+// range of 64-voxel K-steps (boxes of the V grid); rows are 16 groups of 8
+// input channels (one tap each), both operands MN-major, results added to
+// FP32 dW with atomics.  A maps are stride-2 views for KIND_DOWN, B maps for
+// KIND_UP; all others are chunk-plane maps.
 struct WgradParams {
     CUtensorMap amaps[8];
     CUtensorMap bmaps[8];
     int mode;                       // KIND_*
     int kc_total, kc0, n_groups, ones_group;
-    int V_B, V_D, V_H, V_W;
+    int kv;                         // voxels per K-step (64 or 128): a group's block is kv * 16 bytes
+    int ea, eb;                     // chunk planes per A / B box (1 for stride-2 views)
+    TileGrid g;
     int ksteps_total, ksteps_per_cta, n, stages;
     uint32_t a_stage_bytes, b_stage_bytes, stage_bytes;
-    uint32_t idesc, lbo, sbo;
+    uint32_t idesc;
     float* dw;                      // [taps][kc_total * 8][n]
     float* db;                      // [n]
     int* err;

@@ -6,8 +6,9 @@ codes.  There is no CPU fallback: if ``libspnn.so`` has not been built,
 :func:`load` raises, and without a GPU the calls return ``SPNN_ECUDA``.
 
 Function names follow include/spnn.h.  Tensors are torch CUDA tensors:
-activations ``torch.bfloat16`` channels-last (B, D, H, W, C), weights and
-gradients ``torch.float32``.  Streams default to torch's current stream.
+activations ``torch.bfloat16`` in chunk planes, shape (C/8, B, D, H, W, 8)
+(see :func:`to_planes` / :func:`from_planes`), weights and gradients
+``torch.float32``.  Streams default to torch's current stream.
 """
 from __future__ import annotations
 
@@ -90,6 +91,27 @@ def declared_symbols():
     return sorted(set(re.findall(r"\b(spnn_\w+)\s*\(", txt)) - {"spnn_unet_t"})
 
 
+def to_planes(x):
+    """(B, D, H, W, C) tensor -> contiguous chunk planes (C/8, B, D, H, W, 8)."""
+    B, D, H, W, C = x.shape
+    return x.reshape(B, D, H, W, C // 8, 8).permute(4, 0, 1, 2, 3, 5).contiguous()
+
+
+def from_planes(x):
+    """Chunk planes (C/8, B, D, H, W, 8) -> (B, D, H, W, C)."""
+    C8, B, D, H, W, _ = x.shape
+    return x.permute(1, 2, 3, 4, 0, 5).reshape(B, D, H, W, C8 * 8)
+
+
+def planes_empty(B, D, H, W, C, dtype=None):
+    import torch
+    return torch.zeros((C // 8, B, D, H, W, 8), dtype=dtype or torch.bfloat16, device="cuda")
+
+
+def _channels(t):
+    return 0 if t is None else t.shape[0] * 8
+
+
 def _check(rc: int):
     if rc != SPNN_OK:
         raise SpnnError(rc, load().spnn_last_error().decode())
@@ -125,8 +147,7 @@ def spnn_pack_weights(kind, cin, cout, which, w, packed, stream=None):
 def spnn_layer_forward(kind, grid, x0, x1, packed, bias, cout, relu, y, head_w=None, head_b=None,
                        head_out=None, stream=None):
     B, D, H, W = grid
-    c0 = x0.shape[-1]
-    c1 = 0 if x1 is None else x1.shape[-1]
+    c0, c1 = _channels(x0), _channels(x1)
     _check(load().spnn_layer_forward(kind, B, D, H, W, _ptr(x0), c0, _ptr(x1), c1, _ptr(packed), _ptr(bias),
                                      cout, int(relu), _ptr(y), _ptr(head_w), _ptr(head_b), _ptr(head_out),
                                      _stream(stream)))
@@ -135,16 +156,15 @@ def spnn_layer_forward(kind, grid, x0, x1, packed, bias, cout, relu, y, head_w=N
 def spnn_layer_dgrad(kind, grid, dy, packed, c0, c1, dx0, addend0=None, mask0=None, dx1=None, addend1=None,
                      mask1=None, stream=None):
     B, D, H, W = grid
-    _check(load().spnn_layer_dgrad(kind, B, D, H, W, _ptr(dy), dy.shape[-1], _ptr(packed), c0, c1, _ptr(dx0),
+    _check(load().spnn_layer_dgrad(kind, B, D, H, W, _ptr(dy), _channels(dy), _ptr(packed), c0, c1, _ptr(dx0),
                                    _ptr(addend0), _ptr(mask0), _ptr(dx1), _ptr(addend1), _ptr(mask1),
                                    _stream(stream)))
 
 
 def spnn_layer_wgrad(kind, grid, x0, x1, dy, dw, db=None, stream=None):
     B, D, H, W = grid
-    c0 = x0.shape[-1]
-    c1 = 0 if x1 is None else x1.shape[-1]
-    _check(load().spnn_layer_wgrad(kind, B, D, H, W, _ptr(x0), c0, _ptr(x1), c1, _ptr(dy), dy.shape[-1],
+    c0, c1 = _channels(x0), _channels(x1)
+    _check(load().spnn_layer_wgrad(kind, B, D, H, W, _ptr(x0), c0, _ptr(x1), c1, _ptr(dy), _channels(dy),
                                    _ptr(dw), _ptr(db), _stream(stream)))
 
 
@@ -203,7 +223,8 @@ class UNet:
         return a
 
     def forward(self, x, pred, stream=None):
-        _check(load().spnn_unet_forward(self._h, _ptr(x), x.shape[0], _ptr(pred), _stream(stream)))
+        """x: input features in chunk planes (2, B, n, n, n, 8); pred FP32 (B, n, n, n)."""
+        _check(load().spnn_unet_forward(self._h, _ptr(x), pred.shape[0], _ptr(pred), _stream(stream)))
 
     def backward(self, target, loss=None, stream=None):
         _check(load().spnn_unet_backward(self._h, _ptr(target), target.shape[0], _ptr(loss), _stream(stream)))
@@ -212,11 +233,12 @@ class UNet:
         _check(load().spnn_unet_adam(self._h, lr, beta1, beta2, eps, _stream(stream)))
 
     def activation(self, layer: int, batch: int, stream=None):
-        """Copy of a layer's BF16 output, torch (batch, e, e, e, C)."""
+        """Copy of a layer's BF16 output in chunk planes (C/8, batch, e, e, e, 8)."""
         import torch
         e, c = _I(), _I()
         _check(load().spnn_unet_layer_shape(self._h, layer, ctypes.byref(e), ctypes.byref(c)))
-        out = torch.empty((batch, e.value, e.value, e.value, c.value), dtype=torch.bfloat16, device="cuda")
+        out = torch.empty((c.value // 8, batch, e.value, e.value, e.value, 8), dtype=torch.bfloat16,
+                          device="cuda")
         _check(load().spnn_unet_copy_activation(self._h, layer, batch, _ptr(out), _stream(stream)))
         return out
 

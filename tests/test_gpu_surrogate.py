@@ -12,6 +12,7 @@ import pytest
 import torch
 
 from oracle import unet_oracle as U
+from paper_2604_13929_gb300 import spnn as SP
 
 pytestmark = pytest.mark.gpu
 
@@ -24,11 +25,20 @@ def S():
 
 
 def bf(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda().to(torch.bfloat16)
+    """(B, D, H, W, C) values -> BF16 activation in chunk planes on the GPU."""
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda().to(torch.bfloat16)
+    return SP.to_planes(t)
 
 
 def f64(t):
+    """GPU tensor -> float64 numpy; chunk-plane activations come back as (B, D, H, W, C)."""
+    if t.dim() == 6:
+        t = SP.from_planes(t)
     return t.float().cpu().numpy().astype(np.float64)
+
+
+def zeros_act(B, D, H, W, C):
+    return SP.planes_empty(B, D, H, W, C)
 
 
 def w_bf(w):
@@ -61,7 +71,7 @@ def test_conv3_forward_concat_bias_relu(S):
     x0, x1 = bf(rnd(rng, (B, D, H, W, c0))), bf(rnd(rng, (B, D, H, W, c1)))
     w = rnd(rng, (27, c0 + c1, co), 0.1)
     b = rnd(rng, co, 0.5)
-    y = torch.zeros((B, D, H, W, co), dtype=torch.bfloat16, device="cuda")
+    y = zeros_act(B, D, H, W, co)
     S.spnn_layer_forward(S.CONV3, (B, D, H, W), x0, x1, packed(S, 0, c0 + c1, co, 0, w),
                          torch.tensor(b, dtype=torch.float32, device="cuda"), co, True, y)
     S.spnn_status()
@@ -77,7 +87,7 @@ def test_conv3_fused_head(S):
     x = bf(rnd(rng, (B, D, H, W, c0)))
     w = rnd(rng, (27, c0, co), 0.1)
     hw = rnd(rng, co)
-    y = torch.zeros((B, D, H, W, co), dtype=torch.bfloat16, device="cuda")
+    y = zeros_act(B, D, H, W, co)
     out = torch.zeros((B, D, H, W), dtype=torch.float32, device="cuda")
     hwt = torch.tensor(hw, dtype=torch.float32, device="cuda")
     hb = torch.tensor([0.25], dtype=torch.float32, device="cuda")
@@ -97,7 +107,7 @@ def test_down_forward(S):
     x = bf(rnd(rng, (B, D, H, W, c0)))
     w = rnd(rng, (8, c0, co), 0.2)
     b = rnd(rng, co, 0.5)
-    y = torch.zeros((B, D // 2, H // 2, W // 2, co), dtype=torch.bfloat16, device="cuda")
+    y = zeros_act(B, D // 2, H // 2, W // 2, co)
     S.spnn_layer_forward(S.DOWN, (B, D, H, W), x, None, packed(S, 1, c0, co, 0, w),
                          torch.tensor(b, dtype=torch.float32, device="cuda"), co, True, y)
     S.spnn_status()
@@ -111,7 +121,7 @@ def test_up_forward_two_column_tiles(S):
     x = bf(rnd(rng, (B, D, H, W, c0)))
     w = rnd(rng, (8, c0, co), 0.2)
     b = rnd(rng, co, 0.5)
-    y = torch.zeros((B, 2 * D, 2 * H, 2 * W, co), dtype=torch.bfloat16, device="cuda")
+    y = zeros_act(B, 2 * D, 2 * H, 2 * W, co)
     S.spnn_layer_forward(S.UP, (B, D, H, W), x, None, packed(S, 2, c0, co, 0, w),
                          torch.tensor(b, dtype=torch.float32, device="cuda"), co, False, y)
     S.spnn_status()
@@ -127,8 +137,8 @@ def test_conv3_dgrad_split_mask_addend(S):
     w = rnd(rng, (27, c0 + c1, co), 0.1)
     mask0 = bf(rnd(rng, (B, D, H, W, c0)))
     add1 = bf(rnd(rng, (B, D, H, W, c1)))
-    dx0 = torch.zeros((B, D, H, W, c0), dtype=torch.bfloat16, device="cuda")
-    dx1 = torch.zeros((B, D, H, W, c1), dtype=torch.bfloat16, device="cuda")
+    dx0 = zeros_act(B, D, H, W, c0)
+    dx1 = zeros_act(B, D, H, W, c1)
     S.spnn_layer_dgrad(S.CONV3, (B, D, H, W), dy, packed(S, 0, c0 + c1, co, 1, w), c0, c1, dx0, mask0=mask0,
                        dx1=dx1, addend1=add1)
     S.spnn_status()
@@ -145,7 +155,7 @@ def test_down_dgrad_scatter(S):
     w = rnd(rng, (8, c0, co), 0.2)
     add = bf(rnd(rng, (B, D, H, W, c0)))
     mask = bf(rnd(rng, (B, D, H, W, c0)))
-    dx = torch.zeros((B, D, H, W, c0), dtype=torch.bfloat16, device="cuda")
+    dx = zeros_act(B, D, H, W, c0)
     S.spnn_layer_dgrad(S.DOWN, (B, D, H, W), dy, packed(S, 1, c0, co, 1, w), c0, 0, dx, addend0=add, mask0=mask)
     S.spnn_status()
     ref = (U.down_dgrad(f64(dy), w_bf(w)) + f64(add)) * (f64(mask) > 0)
@@ -158,7 +168,7 @@ def test_up_dgrad_gather(S):
     B, D, H, W, c0, co = 2, 4, 4, 8, 32, 64
     dy = bf(rnd(rng, (B, 2 * D, 2 * H, 2 * W, co)))
     w = rnd(rng, (8, c0, co), 0.2)
-    dx = torch.zeros((B, D, H, W, c0), dtype=torch.bfloat16, device="cuda")
+    dx = zeros_act(B, D, H, W, c0)
     S.spnn_layer_dgrad(S.UP, (B, D, H, W), dy, packed(S, 2, c0, co, 1, w), c0, 0, dx)
     S.spnn_status()
     check(f64(dx), U.up_dgrad(f64(dy), w_bf(w)), U.up_dgrad(np.abs(f64(dy)), np.abs(w_bf(w))), what="up dgrad")
@@ -209,7 +219,7 @@ def test_pack_input_log_fluence_profiles(S):
     B, D, H, W = 3, 8, 4, 8
     mask = (rng.random((B, D, H, W)) < 0.6).astype(np.uint8)
     optics = np.array([[0.5, 0.005, 0.7], [1.9, 0.04, 0.0], [0.11, 0.0012, 0.89]], dtype=np.float32)
-    x = torch.zeros((B, D, H, W, 16), dtype=torch.bfloat16, device="cuda")
+    x = zeros_act(B, D, H, W, 16)
     S.spnn_pack_input(torch.from_numpy(mask).cuda(), torch.from_numpy(optics).cuda(), x)
     ref = U.pack_input(mask, optics[:, 0].astype(np.float64), optics[:, 1].astype(np.float64),
                        optics[:, 2].astype(np.float64))
@@ -246,7 +256,7 @@ def net_run(S):
     mask = (rng.random((BATCH, N, N, N)) < 0.7).astype(np.uint8)
     optics = np.stack([rng.uniform(0.1, 2.0, BATCH), rng.uniform(0.001, 0.05, BATCH),
                        rng.uniform(0.0, 0.9, BATCH)], axis=1).astype(np.float32)
-    x = torch.zeros((BATCH, N, N, N, 16), dtype=torch.bfloat16, device="cuda")
+    x = zeros_act(BATCH, N, N, N, 16)
     S.spnn_pack_input(torch.from_numpy(mask).cuda(), torch.from_numpy(optics).cuda(), x)
     pred = torch.zeros((BATCH, N, N, N), dtype=torch.float32, device="cuda")
     net.forward(x, pred)
@@ -333,7 +343,7 @@ def test_unet_training_reduces_loss(S):
     net.set_params(S.flatten_params(U.init_params(C0, 4), C0))
     mask = (rng.random((BATCH, N, N, N)) < 0.7).astype(np.uint8)
     optics = np.tile(np.array([[0.5, 0.005, 0.7]], dtype=np.float32), (BATCH, 1))
-    x = torch.zeros((BATCH, N, N, N, 16), dtype=torch.bfloat16, device="cuda")
+    x = zeros_act(BATCH, N, N, N, 16)
     S.spnn_pack_input(torch.from_numpy(mask).cuda(), torch.from_numpy(optics).cuda(), x)
     z = (np.arange(N) + 0.5) / N
     tgt = -2.0 * z[None, :, None, None] + 0.3 * mask
