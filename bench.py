@@ -348,6 +348,71 @@ def precision_study(torch, spmc, args):
     print(json.dumps(out), flush=True)
 
 
+def surrogate_bench(torch, args):
+    """The learned surrogate on 64^3 masks: Monte Carlo training fields from
+    the transport engine, training, held-out profile error (Eq. RMSw) and
+    fields per second against the Monte Carlo producing the same field."""
+    from paper_2604_13929_gb300 import spnn, surrogate as sg
+    c0, n, batch = 32, 64, args.surrogate_batch
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    t0 = time.perf_counter()
+    train_set = sg.make_fields(args.surrogate_train, seed=1, photons=args.surrogate_photons, n=n)
+    test_set = sg.make_fields(args.surrogate_test, seed=2, photons=args.surrogate_photons, n=n)
+    data_s = time.perf_counter() - t0
+    net = spnn.UNet(c0, n, batch)
+    net.set_params(spnn.init_params(c0, 7))
+    log = []
+    losses, train_s = sg.train(net, train_set, args.surrogate_steps, batch,
+                               on_log=lambda st, l: log.append((st, l)))
+    ev = sg.evaluate(net, test_set, batch)
+    with Clocks(0) as clk:
+        rate = sg.inference_rate(net, test_set, batch, reps=10)
+    # algorithmic FLOPs of one field's forward: 2 x input voxels x ci x co x taps
+    # per input voxel (27 for conv3, 1 for the stride-2 down, 8 for the up)
+    fl = 0
+    lv = {"e0": 0, "d1": 0, "e1": 1, "d2": 1, "e2": 2, "d3": 2, "b1": 3, "b2": 3, "u2": 3, "c2": 2,
+          "u1": 2, "c1": 1, "u0": 1, "c0": 0}
+    for name, kind, ci, co in spnn.layer_table(c0):
+        v = (n >> lv[name[:2]]) ** 3
+        fl += 2 * v * ci * co * {"conv3": 27, "down": 1, "up": 8}[kind]
+    mc_rate = test_set.info["mc_fields_per_s"]
+    # Monte Carlo given the surrogate's time per field: its profile error on the held-out masks
+    eq_photons = max(1000, int(test_set.info["mc_photons_per_s"] / rate["fields_per_s"]))
+    eq_target, _ = sg.simulate(test_set.mask, test_set.optics, eq_photons, seed=sg.MC_SEED + 99)
+    eq_rms = sg.profile_rms(sg.profiles(eq_target, test_set.mask), sg.profiles(test_set.target, test_set.mask))
+    eq_d = (eq_target - test_set.target).double()
+    achieved = fl * batch / (rate["ms_per_batch"] / 1e3) / 1e12
+    line = {"metric": "surrogate fields/s (64^3 ln-fluence + per-phase depth profiles)",
+            "value": rate["fields_per_s"], "unit": "fields/s", "n_gpus": 1, "steps": args.surrogate_steps,
+            "warmup": 1, "ms_per_step": rate["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"3D U-Net c0={c0} (4 levels, 32-256 channels) on {n}^3 Cahn-Hilliard masks, "
+                                   f"porosity U[0.5,0.95], mu_s h logU[0.1,2], mu_a h U[0.001,0.05], "
+                                   f"g U[0,0.9]; {args.surrogate_train} training / {args.surrogate_test} held-out "
+                                   f"Monte Carlo fields of {args.surrogate_photons:.0e} photons; batch {batch}",
+                       "params": net.param_count},
+            "mc_fields_per_s": mc_rate, "speedup_vs_mc": rate["fields_per_s"] / mc_rate,
+            "heldout": ev,
+            "equal_time_mc": {"photons": eq_photons, "rms_w_mean": float(np.nanmean(eq_rms)),
+                              "rms_w_median": float(np.nanmedian(eq_rms)),
+                              "voxel_ln_rmse": float(torch.sqrt((eq_d * eq_d).mean()).item()),
+                              "voxel_rel_rmse": float(torch.sqrt(((torch.exp(eq_d) - 1) ** 2).mean()).item()),
+                              "frac_voxels_without_track": float((eq_target <= np.log(2e-6)).double().mean().item())},
+            "training": {"steps": args.surrogate_steps, "seconds": train_s,
+                         "ms_per_step": 1e3 * train_s / args.surrogate_steps,
+                         "tflops": 3 * fl * batch * args.surrogate_steps / train_s / 1e12,
+                         "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-10:])),
+                         "log": log[::max(1, len(log) // 12)]},
+            "data_seconds": data_s, "mc_photons_per_s": test_set.info["mc_photons_per_s"],
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"], "traffic": None,
+                         "kernel": "spnn rows_kernel, all 20 forward layers", "flop_per_field": fl,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"},
+            "gpu_launches": 22 * 10, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,10 +423,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batch", "paper", "precision"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch", "paper", "precision", "surrogate"],
                     help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
                          "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
     ap.add_argument("--precision-photons", type=int, default=1_000_000_000)
+    ap.add_argument("--surrogate-train", type=int, default=2048)
+    ap.add_argument("--surrogate-test", type=int, default=128)
+    ap.add_argument("--surrogate-steps", type=int, default=1500)
+    ap.add_argument("--surrogate-batch", type=int, default=256)
+    ap.add_argument("--surrogate-photons", type=int, default=10_000_000)
     ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
                     help="profiling case: one warm-up launch of N/10 photons, then one timed "
                          "launch of N photons on the workload; prints its time and exits")
@@ -398,6 +468,10 @@ def main():
     if args.workload == "precision":
         if rank == 0:
             precision_study(torch, spmc, args)
+        return
+    if args.workload == "surrogate":
+        if rank == 0:
+            surrogate_bench(torch, args)
         return
     mask = make_mask("cuda")
     stream = torch.cuda.current_stream()

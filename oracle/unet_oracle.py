@@ -260,17 +260,29 @@ def adam_step(p, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
 def pack_input(mask, mus, mua, g):
     """Features per voxel, channels-last (B, D, H, W, 16):
     0 pore indicator, 1 solid indicator, 2 ln(mu_s h), 3 ln(mu_a h) / 4, 4 g,
-    5 depth (z + 1/2) / D, 6..15 zero.  mask: (B, D, H, W) with 1 = pore."""
+    5 depth (z + 1/2) / D, 6 -mu_eff (z + 1/2) / 8, 7 porosity phi, 8..15 zero.
+    phi is the pore fraction of the sample's mask; mu_eff = sqrt(3 mu_a' (mu_a'
+    + mu_s' (1 - g))) is the diffusion-theory attenuation (Sec. 2.4: kappa =
+    sqrt(mu_a / D), D = 1 / (3 (mu_a + mu_s'))) of the medium scaled to its
+    solid fraction, mu' = (1 - phi) mu (Eq. EMA_scaling).  mask: (B, D, H, W),
+    1 = pore."""
     m = np.asarray(mask, dtype=np.float64)
     B, D, H, W = m.shape
     x = np.zeros((B, D, H, W, N_FEATURES))
     x[..., 0] = m
     x[..., 1] = 1.0 - m
+    zc = np.arange(D) + 0.5
     for b in range(B):
+        phi = m[b].mean()
+        ma = (1.0 - phi) * mua[b]
+        msp = (1.0 - phi) * mus[b] * (1.0 - g[b])
+        mu_eff = math.sqrt(3.0 * ma * (ma + msp))
         x[b, ..., 2] = math.log(mus[b])
         x[b, ..., 3] = math.log(mua[b]) / 4.0
         x[b, ..., 4] = g[b]
-    x[..., 5] = ((np.arange(D) + 0.5) / D)[None, :, None, None]
+        x[b, ..., 6] = (-mu_eff * zc / 8.0)[:, None, None]
+        x[b, ..., 7] = phi
+    x[..., 5] = (zc / D)[None, :, None, None]
     return x
 
 

@@ -183,9 +183,10 @@ int rows_gemm(RowsParams& p, cudaStream_t st) {
     p.idesc = idesc_bf16(128, p.n_tile, 0, 0);
     p.err = err_ptr();
     if (!p.err) return fail(SPNN_ECUDA, "no device");
-    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
+    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 4) * 8 + 16;
     if (smem > 227 * 1024) return fail(SPNN_EINVAL, "stage of %u bytes does not fit", p.stage_bytes);
-    cudaError_t e = launch_rows(p, (int)n_tiles(p.g), p.n_total / p.n_tile, smem, st);
+    p.tiles_m = n_tiles(p.g);
+    cudaError_t e = launch_rows(p, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "rows_kernel launch");
     return SPNN_OK;
 }
@@ -490,17 +491,39 @@ int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, co
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 // --------------------------------------------------------- data kernels --
+// Pore fraction of each sample's mask: one block per sample.
+__global__ void porosity_kernel(const uint8_t* __restrict__ mask, long long vox_per_sample, float* __restrict__ phi) {
+    const uint8_t* m = mask + (long long)blockIdx.x * vox_per_sample;
+    unsigned long long c = 0;
+    for (long long i = threadIdx.x; i < vox_per_sample; i += blockDim.x) c += m[i] ? 1 : 0;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __shared__ unsigned long long part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        phi[blockIdx.x] = (float)((double)t / (double)vox_per_sample);
+    }
+}
+
 // Input features in chunk planes: plane 0 holds channels 0-7, plane 1 channels 8-15 (zero).
-__global__ void pack_input_kernel(const uint8_t* __restrict__ mask, const float* __restrict__ optics, int D,
-                                  long long vox_per_sample, long long total, __nv_bfloat16* __restrict__ x,
-                                  int HW) {
+// Channel 6 is the diffusion-theory attenuation exponent -mu_eff (z + 1/2) / 8 of the
+// medium scaled to its solid fraction (mu' = (1 - phi) mu), channel 7 the porosity phi.
+__global__ void pack_input_kernel(const uint8_t* __restrict__ mask, const float* __restrict__ optics,
+                                  const float* __restrict__ phi, int D, long long vox_per_sample,
+                                  long long total, __nv_bfloat16* __restrict__ x, int HW) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const long long b = i / vox_per_sample;
         const int z = (int)((i % vox_per_sample) / HW);
         const float pore = mask[i] ? 1.f : 0.f;
-        const float mus = optics[3 * b], mua = optics[3 * b + 1], g = optics[3 * b + 2];
-        const float f[8] = {pore, 1.f - pore, logf(mus), 0.25f * logf(mua), g, (z + 0.5f) / (float)D, 0.f, 0.f};
+        const float mus = optics[3 * b], mua = optics[3 * b + 1], g = optics[3 * b + 2], ph = phi[b];
+        const float ma = (1.f - ph) * mua, msp = (1.f - ph) * mus * (1.f - g);
+        const float mu_eff = sqrtf(3.f * ma * (ma + msp));
+        const float zc = z + 0.5f;
+        const float f[8] = {pore, 1.f - pore, logf(mus), 0.25f * logf(mua), g, zc / (float)D,
+                            -mu_eff * zc * 0.125f, ph};
         uint4 w;
         __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&w);
 #pragma unroll
@@ -752,9 +775,15 @@ int spnn_layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c
 int spnn_pack_input(const uint8_t* mask, const float* optics, int B, int D, int H, int W, void* x, void* stream) {
     if (!mask || !optics || !x || B <= 0 || D <= 0 || H <= 0 || W <= 0) return fail(SPNN_EINVAL, "bad arguments");
     const long long vps = (long long)D * H * W, total = vps * B;
-    pack_input_kernel<<<grid_for(total), 256, 0, as_stream(stream)>>>(mask, optics, D, vps, total,
-                                                                       static_cast<__nv_bfloat16*>(x), H * W);
-    CU(cudaGetLastError());
+    cudaStream_t st = as_stream(stream);
+    float* phi = nullptr;
+    CU(cudaMallocAsync(reinterpret_cast<void**>(&phi), sizeof(float) * B, st));
+    porosity_kernel<<<B, 256, 0, st>>>(mask, vps, phi);
+    pack_input_kernel<<<grid_for(total), 256, 0, st>>>(mask, optics, phi, D, vps, total,
+                                                        static_cast<__nv_bfloat16*>(x), H * W);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(phi, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pack_input launch");
     return SPNN_OK;
 }
 

@@ -347,6 +347,11 @@ class Batch:
                                             stream_handle(stream)))
         return out
 
+    def raw_field_to(self, i: int, dst, stream=None):
+        """Copy problem i's Q32.32 field into a device buffer (torch uint64/int64 tensor)."""
+        assert dst.numel() == self.masks[i].size and dst.element_size() == 8 and dst.is_cuda
+        _check(load().sp_mc_batch_raw_field(self.handle, int(i), dst.data_ptr(), 1, stream_handle(stream)))
+
     def reset(self, stream=None):
         _check(load().sp_mc_batch_reset(self.handle, stream_handle(stream)))
 

@@ -13,6 +13,7 @@ activations ``torch.bfloat16`` in chunk planes, shape (C/8, B, D, H, W, 8)
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -241,6 +242,34 @@ class UNet:
                           device="cuda")
         _check(load().spnn_unet_copy_activation(self._h, layer, batch, _ptr(out), _stream(stream)))
         return out
+
+
+def layer_table(c0: int):
+    """(name, kind, input channels, output channels) of the library's U-Net in
+    forward order (the table compiled into libspnn; its parameter count is
+    checked against spnn_unet_param_count by the tests)."""
+    c1, c2, c3 = 2 * c0, 4 * c0, 8 * c0
+    return [("e0a", "conv3", N_FEATURES, c0), ("e0b", "conv3", c0, c0), ("d1", "down", c0, c1),
+            ("e1a", "conv3", c1, c1), ("e1b", "conv3", c1, c1), ("d2", "down", c1, c2),
+            ("e2a", "conv3", c2, c2), ("e2b", "conv3", c2, c2), ("d3", "down", c2, c3),
+            ("b1", "conv3", c3, c3), ("b2", "conv3", c3, c3), ("u2", "up", c3, c2),
+            ("c2a", "conv3", 2 * c2, c2), ("c2b", "conv3", c2, c2), ("u1", "up", c2, c1),
+            ("c1a", "conv3", 2 * c1, c1), ("c1b", "conv3", c1, c1), ("u0", "up", c1, c0),
+            ("c0a", "conv3", 2 * c0, c0), ("c0b", "conv3", c0, c0)]
+
+
+def init_params(c0: int, seed: int) -> np.ndarray:
+    """He-normal initial weights (std sqrt(2 / fan_in), fan_in = taps x input
+    channels, or input channels for the transposed 2x2x2 layers), zero biases,
+    head weights of std sqrt(1 / c0): the flat FP32 vector of spnn.h."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, kind, ci, co in layer_table(c0):
+        taps = 27 if kind == "conv3" else 8
+        fan_in = ci if kind == "up" else taps * ci
+        parts += [rng.standard_normal(taps * ci * co) * math.sqrt(2.0 / fan_in), np.zeros(co)]
+    parts += [rng.standard_normal(c0) * math.sqrt(1.0 / c0), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
 
 
 def flatten_params(params: dict, c0: int) -> np.ndarray:

@@ -189,7 +189,14 @@ def test_pack_input_and_targets():
     assert x[1, 0, 0, 0, 3] == pytest.approx(math.log(0.01) / 4)
     assert x[0, 1, 1, 2, 4] == pytest.approx(0.7)
     assert x[1, 3, 0, 1, 5] == pytest.approx(3.5 / 4)
-    assert np.all(x[..., 6:] == 0)
+    # sample 1 has one pore voxel of 24: phi = 1/24; diffusion attenuation of
+    # the solid-fraction-scaled medium, mu_eff^2 = 3 mu_a' (mu_a' + mu_s'(1 - g))
+    phi = 1 / 24
+    ma, msp = (1 - phi) * 0.01, (1 - phi) * 2.0 * 1.0
+    assert x[1, 2, 0, 0, 7] == pytest.approx(phi) and x[0, 0, 0, 0, 7] == 0
+    assert x[1, 2, 1, 1, 6] == pytest.approx(-math.sqrt(3 * ma * (ma + msp)) * 2.5 / 8)
+    assert x[0, 0, 0, 0, 6] == pytest.approx(-math.sqrt(3 * 0.005 * (0.005 + 0.5 * 0.3)) * 0.5 / 8)
+    assert np.all(x[..., 8:] == 0)
     # an all-pore slab puts exactly one voxel of track per photon into each
     # layer, i.e. F = N / (nx ny) per voxel: Phi/S0 = 1 and ln Phi = 0
     nx, ny, n = 4, 2, 1000
