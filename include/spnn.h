@@ -108,7 +108,11 @@ int spnn_layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c
 /*
  * Input features, BF16 chunk planes [2][B][D][H][W][8] (16 channels):
  * 0 pore (mask == 1), 1 solid, 2 ln(mu_s h), 3 ln(mu_a h)/4, 4 g,
- * 5 (z + 1/2)/D, 6..15 zero.
+ * 5 (z + 1/2)/D, 6 -mu_eff (z + 1/2)/8, 7 porosity phi, 8..15 zero, where phi
+ * is the sample's pore fraction and mu_eff = sqrt(3 mu_a' (mu_a' + mu_s'(1-g)))
+ * the diffusion attenuation (Sec. 2.4) of the medium scaled to its solid
+ * fraction, mu' = (1 - phi) mu (Eq. EMA_scaling).  Uses a B-float scratch
+ * from the stream-ordered allocator.
  * mask: uint8 (B, D, H, W), 1 = pore;  optics: FP32 (B, 3) = (mu_s h, mu_a h, g).
  */
 int spnn_pack_input(const uint8_t* mask, const float* optics, int B, int D, int H, int W, void* x, void* stream);

@@ -183,10 +183,9 @@ int rows_gemm(RowsParams& p, cudaStream_t st) {
     p.idesc = idesc_bf16(128, p.n_tile, 0, 0);
     p.err = err_ptr();
     if (!p.err) return fail(SPNN_ECUDA, "no device");
-    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 4) * 8 + 16;
+    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
     if (smem > 227 * 1024) return fail(SPNN_EINVAL, "stage of %u bytes does not fit", p.stage_bytes);
-    p.tiles_m = n_tiles(p.g);
-    cudaError_t e = launch_rows(p, smem, st);
+    cudaError_t e = launch_rows(p, (int)n_tiles(p.g), p.n_total / p.n_tile, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "rows_kernel launch");
     return SPNN_OK;
 }

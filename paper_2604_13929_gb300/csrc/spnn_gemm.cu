@@ -48,24 +48,20 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
     const int S = p.stages;
-    // barriers: full[S], empty[S], acc_full[2], acc_empty[2]; then the TMEM slot
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = smem_u32(bars);
-    const uint32_t accf = bar0 + 16u * S, acce = accf + 16u;
+    const uint32_t done = bar0 + 16u * S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = tmem_cols(2 * p.n_tile);   // two accumulators: tile i and tile i + 1
+    const uint32_t ncols = tmem_cols(p.n_tile);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(bar0 + 8u * s, 1);
             mbar_init(bar0 + 8u * (S + s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(accf + 8u * b, 1);
-            mbar_init(acce + 8u * b, 4);   // one arrival per epilogue warp
-        }
+        mbar_init(done, 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -77,140 +73,109 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int n_n = p.n_total / p.n_tile;
-    const long long total = p.tiles_m * n_n;
+    int x0, y0, z0, b0;
+    tile_origin(p.g, blockIdx.x, x0, y0, z0, b0);
+
     const bool conv = p.tap_mode == TAP_SHIFT3;
     if (warp == 0) {
         if (lane == 0) {
             const int gpt = conv ? p.kc_total / p.E : p.kc_total / p.kc_step;
             const uint32_t tx = p.a_stage_bytes + p.b_stage_bytes;
-            long long kk = 0;
-            bool ok = true;
-            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const long long tm = t / n_n;
-                const int tn = (int)(t % n_n);
-                int x0, y0, z0, b0;
-                tile_origin(p.g, tm, x0, y0, z0, b0);
-                for (int k = 0; k < p.ksteps; ++k, ++kk) {
-                    const int s = (int)(kk % S);
-                    const uint32_t r = (uint32_t)(kk / S);
-                    const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
-                    if (kk >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
-                        atomicOr(p.err, ERR_TIMEOUT);
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(full, tx);
-                    const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-                    const int tap = k / gpt, g = k % gpt;
-                    if (conv) {
-                        // tap = x-shift index, g = block of E chunk planes
-                        const int dx = tap - 1, kc = g * p.E;
-                        const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
-                        if (p.halo) {
-                            tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 + dx), y0 - 1, z0 - 1, b0, c8);
-                        } else {
-                            for (int t9 = 0; t9 < 9; ++t9)
-                                tma_load_5d(a_dst + (uint32_t)(t9 * p.E) * 2048u, &p.maps[mi], full,
-                                            8 * (x0 + dx), y0 + (t9 % 3) - 1, z0 + (t9 / 3) - 1, b0, c8);
-                        }
-                        const __nv_bfloat16* src =
-                            p.wpack + ((size_t)(tn * 3 + tap) * p.kc_total + kc) * 9 * p.n_tile * 8;
-                        bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
+            for (int k = 0; k < p.ksteps; ++k) {
+                const int s = k % S;
+                const uint32_t r = (uint32_t)(k / S);
+                const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
+                if (k >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
+                    atomicOr(p.err, ERR_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(full, tx);
+                const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
+                const int tap = k / gpt, g = k % gpt;
+                if (conv) {
+                    // tap = x-shift index, g = block of E chunk planes
+                    const int dx = tap - 1, kc = g * p.E;
+                    const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
+                    if (p.halo) {
+                        tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 + dx), y0 - 1, z0 - 1, b0, c8);
                     } else {
-                        if (p.tap_mode == TAP_MAP) {
-                            for (int j = 0; j < p.kc_step; ++j)
-                                load_box(a_dst + 2048u * j, &p.maps[tap], full, true, g * p.kc_step + j, x0, y0,
-                                         z0, b0, p.g.B);
-                        } else {
-                            // TAP_NONE: one box of kc_step chunk planes
-                            tma_load_5d(a_dst, &p.maps[0], full, 8 * x0, y0, z0, b0, g * p.kc_step);
-                        }
-                        const __nv_bfloat16* src =
-                            p.wpack + ((size_t)(tn * p.n_taps + tap) * p.kc_total + (size_t)g * p.kc_step) *
-                                          p.n_tile * 8;
-                        bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
+                        for (int t9 = 0; t9 < 9; ++t9)
+                            tma_load_5d(a_dst + (uint32_t)(t9 * p.E) * 2048u, &p.maps[mi], full, 8 * (x0 + dx),
+                                        y0 + (t9 % 3) - 1, z0 + (t9 / 3) - 1, b0, c8);
                     }
+                    const __nv_bfloat16* src =
+                        p.wpack + ((size_t)(blockIdx.y * 3 + tap) * p.kc_total + kc) * 9 * p.n_tile * 8;
+                    bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
+                } else {
+                    if (p.tap_mode == TAP_MAP) {
+                        for (int j = 0; j < p.kc_step; ++j)
+                            load_box(a_dst + 2048u * j, &p.maps[tap], full, true, g * p.kc_step + j, x0, y0, z0,
+                                     b0, p.g.B);
+                    } else {
+                        // TAP_NONE: one box of kc_step chunk planes
+                        tma_load_5d(a_dst, &p.maps[0], full, 8 * x0, y0, z0, b0, g * p.kc_step);
+                    }
+                    const __nv_bfloat16* src =
+                        p.wpack + ((size_t)(blockIdx.y * p.n_taps + tap) * p.kc_total + (size_t)g * p.kc_step) *
+                                      p.n_tile * 8;
+                    bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t nrow = (uint32_t)p.n_tile * 16u;   // bytes of one packed chunk of B
-            long long kk = 0;
-            int i = 0;
-            bool ok = true;
-            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
-                const int buf = i & 1;
-                // the epilogue must have drained this accumulator (tile i - 2)
-                if (i >= 2 && !mbar_wait(acce + 8u * buf, (uint32_t)((i >> 1) - 1) & 1u, kWaitLimitNs)) {
+            for (int k = 0; k < p.ksteps; ++k) {
+                const int s = k % S;
+                const uint32_t r = (uint32_t)(k / S);
+                if (!mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs)) {
                     atomicOr(p.err, ERR_TIMEOUT);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * p.n_tile);
-                for (int k = 0; k < p.ksteps; ++k, ++kk) {
-                    const int s = (int)(kk % S);
-                    const uint32_t r = (uint32_t)(kk / S);
-                    if (!mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs)) {
-                        atomicOr(p.err, ERR_TIMEOUT);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
-                    const uint32_t b0s = a0 + p.a_stage_bytes;
-                    if (conv) {
-                        const uint32_t rowb = (uint32_t)p.g.bx * 16u;
-                        for (int t9 = 0; t9 < 9; ++t9) {
-                            const uint32_t a_tap =
-                                p.halo ? a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb
-                                       : a0 + (uint32_t)(t9 * p.E) * 2048u;
-                            const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
-                            for (int q = 0; q < p.E / 2; ++q) {
-                                const uint64_t ad = smem_desc(a_tap + 2u * q * lbo_a, lbo_a, 128);
-                                const uint64_t bd =
-                                    smem_desc(b0s + (uint32_t)(2 * q * 9 + t9) * nrow, 9u * nrow, 128);
-                                umma_bf16(d, ad, bd, p.idesc, (k > 0 || t9 > 0 || q > 0) ? 1u : 0u);
-                            }
-                        }
-                    } else {
-                        for (int q = 0; q < p.kc_step / 2; ++q) {
-                            const uint64_t ad = smem_desc(a0 + 4096u * q, 2048u, 128);
-                            const uint64_t bd = smem_desc(b0s + 2u * q * nrow, nrow, 128);
-                            umma_bf16(d, ad, bd, p.idesc, (k > 0 || q > 0) ? 1u : 0u);
+                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
+                const uint32_t b0s = a0 + p.a_stage_bytes;
+                if (conv) {
+                    const uint32_t rowb = (uint32_t)p.g.bx * 16u;
+                    for (int t9 = 0; t9 < 9; ++t9) {
+                        const uint32_t a_tap =
+                            p.halo ? a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb
+                                   : a0 + (uint32_t)(t9 * p.E) * 2048u;
+                        const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
+                        for (int i = 0; i < p.E / 2; ++i) {
+                            const uint64_t ad = smem_desc(a_tap + 2u * i * lbo_a, lbo_a, 128);
+                            const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
+                            umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
                         }
                     }
-                    umma_commit(bar0 + 8u * (S + s));
+                } else {
+                    for (int i = 0; i < p.kc_step / 2; ++i) {
+                        const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
+                        const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
+                        umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                    }
                 }
-                umma_commit(accf + 8u * buf);
+                umma_commit(bar0 + 8u * (S + s));
             }
+            umma_commit(done);
         }
     } else {
         const int q = warp & 3;
         const int r = q * 32 + lane;
-        int i = 0;
-        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const int buf = i & 1;
-            bool ok = mbar_wait(accf + 8u * buf, (uint32_t)(i >> 1) & 1u, kWaitLimitNs);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
-                break;
-            }
+        bool ok = mbar_wait(done, 0, kWaitLimitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+        } else {
             tc_fence_after();
-            const long long tm = t / n_n;
-            const int tn = (int)(t % n_n);
-            int x0, y0, z0, b0;
-            tile_origin(p.g, tm, x0, y0, z0, b0);
             int vx, vy, vz, vb;
             const long long vox = row_voxel(p.g, x0, y0, z0, b0, r, &vx, &vy, &vz, &vb);
             float head_acc = 0.f;
             for (int j = 0; j < p.n_tile / 16; ++j) {
                 uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * p.n_tile + j * 16), v);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 16), v);
                 tmem_wait_ld();
-                const int n0 = tn * p.n_tile + j * 16;
+                const int n0 = blockIdx.y * p.n_tile + j * 16;
                 const EpiDest& d = (n0 < p.split) ? p.d[0] : p.d[1];
                 if (d.out == nullptr) continue;
                 int ch0;
@@ -229,46 +194,42 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 }
                 float f[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[e]);
+                for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
                 if (d.bias) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) f[e] += d.bias[ch0 + e];
+                    for (int i = 0; i < 16; ++i) f[i] += d.bias[ch0 + i];
                 }
                 if (d.addend) {
                     float a[16];
                     load16_planes(d.addend + off, d.plane, a);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) f[e] += a[e];
+                    for (int i = 0; i < 16; ++i) f[i] += a[i];
                 }
                 if (d.relu) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
+                    for (int i = 0; i < 16; ++i) f[i] = fmaxf(f[i], 0.f);
                 }
                 if (d.mask) {
                     float m[16];
                     load16_planes(d.mask + off, d.plane, m);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) f[e] = (m[e] > 0.f) ? f[e] : 0.f;
+                    for (int i = 0; i < 16; ++i) f[i] = (m[i] > 0.f) ? f[i] : 0.f;
                 }
                 uint4 w[2];
                 __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) h[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+                for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
                 *reinterpret_cast<uint4*>(d.out + off) = w[0];
                 *reinterpret_cast<uint4*>(d.out + off + d.plane) = w[1];
                 if (p.head_out) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float2 rb = __bfloat1622float2(h[e]);
-                        head_acc += rb.x * p.head_w[ch0 + 2 * e] + rb.y * p.head_w[ch0 + 2 * e + 1];
+                    for (int i = 0; i < 8; ++i) {
+                        const float2 rb = __bfloat1622float2(h[i]);
+                        head_acc += rb.x * p.head_w[ch0 + 2 * i] + rb.y * p.head_w[ch0 + 2 * i + 1];
                     }
                 }
             }
             if (p.head_out) p.head_out[vox] = head_acc + *p.head_b;
-            // hand the accumulator back to the MMA warp
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce + 8u * buf);
         }
     }
     tc_fence_before();
@@ -452,30 +413,14 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     }
 }
 
-cudaError_t launch_rows(const RowsParams& p, size_t smem, cudaStream_t s) {
+cudaError_t launch_rows(const RowsParams& p, int grid_m, int grid_n, size_t smem, cudaStream_t s) {
     static bool attr = false;
-    static int sms = 0;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         attr = true;
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_kernel, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // resident CTAs must also fit the SM's 512 TMEM columns, or a persistent CTA
-    // would sit in tcgen05.alloc until a neighbour finishes all its tiles
-    const int tmem_fit = 512 / (int)tmem_cols(2 * p.n_tile);
-    if (per_sm > tmem_fit) per_sm = tmem_fit;
-    // persistent: at most one wave of CTAs, each walks tiles blockIdx.x, + gridDim.x, ...
-    const long long total = p.tiles_m * (p.n_total / p.n_tile);
-    const long long wave = (long long)sms * per_sm;
-    const int grid = (int)(total < wave ? total : wave);
-    rows_kernel<<<grid, kThreads, smem, s>>>(p);
+    rows_kernel<<<dim3(grid_m, grid_n), kThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -68,10 +68,8 @@ struct EpiDest {
     int relu;
 };
 
-// Rows GEMM: D[row, n] = sum_k A[row, k] B[n, k]; persistent CTAs walk tiles
-// of 128 rows (the voxels of one box of the row grid) x n_tile columns,
-// double-buffering the TMEM accumulator so one tile's epilogue overlaps the
-// next tile's MMAs; k = (tap, channel), A gathered by TMA boxes from
+// Rows GEMM: D[row, n] = sum_k A[row, k] B[n, k]; rows are the 128 voxels of
+// one box of the row grid, k = (tap, channel), A gathered by TMA boxes from
 // chunk-plane maps (coordinates 8x, y, z, b, c8) or, for TAP_MAP, stride-2
 // views (coordinates 0, x, y, z, c8 * B + b).
 //
@@ -87,7 +85,6 @@ struct RowsParams {
     int halo, E;                    // conv3 only
     uint32_t halo_plane;            // bytes of one chunk plane of the halo box
     TileGrid g;
-    long long tiles_m;              // row tiles; the persistent grid walks tiles_m x (n_total / n_tile)
     int n_tile, n_total, ksteps, stages;
     uint32_t a_stage_bytes, b_stage_bytes, stage_bytes;
     uint32_t idesc;
@@ -120,7 +117,7 @@ struct WgradParams {
     int* err;
 };
 
-cudaError_t launch_rows(const RowsParams& p, size_t smem, cudaStream_t s);
+cudaError_t launch_rows(const RowsParams& p, int grid_m, int grid_n, size_t smem, cudaStream_t s);
 cudaError_t launch_wgrad(const WgradParams& p, dim3 grid, size_t smem, cudaStream_t s);
 // TMEM columns to allocate for n FP32 accumulator columns (a power of two >= 32).
 __host__ __device__ inline uint32_t tmem_cols(int n) {
