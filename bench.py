@@ -174,7 +174,9 @@ def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
     gen_s = time.perf_counter() - t0
     n_each = 10_000_000
     b = spmc.Batch(problems)
-    tuned = b.autotune([n_each // 50] * len(problems), SEED + 7, stream)
+    # the autotuner times each candidate on a tenth of a step: large enough that
+    # per-launch overheads weigh as they do in the timed steps
+    tuned = b.autotune([n_each // 10] * len(problems), SEED + 7, stream)
     for _ in range(args.warmup):
         b.run([n_each] * len(problems), SEED + rank, stream)
     torch.cuda.synchronize()
@@ -213,7 +215,7 @@ def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
                                    "64^3..256^3, porosity U[0.5,0.95], mu_s h logU[0.1,2], "
                                    "mu_a h U[0.001,0.05], g U[0,0.9]; 1e7 photons each per step; "
                                    "one persistent launch per step, CUDA graph replay",
-                       "launch": {k: b.get_option(k) for k in ("threads", "blocks", "compact")},
+                       "launch": {k: b.get_option(k) for k in ("threads", "blocks", "compact", "batch_mode")},
                        "autotune_photons_per_s": tuned, "mask_generation_s": gen_s},
             "voxel_steps_per_s": steps * world / (ms / 1e3),
             "sequential_photons_per_s": seq_rate,

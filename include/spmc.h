@@ -78,9 +78,14 @@ enum sp_option {
     SP_OPT_GRAPH       = 13, /* batched launches only: 1 (default) captures
                                 the launch in a CUDA graph and replays it
                                 while photon counts and seed are unchanged */
-    SP_OPT_LATERAL_BC  = 14  /* 0 (default): periodic x and y; 1: specular
+    SP_OPT_LATERAL_BC  = 14, /* 0 (default): periodic x and y; 1: specular
                                 mirrors on the lateral faces (the paper's
                                 bc = "mmamma", Sec. 2.5)                  */
+    SP_OPT_BATCH_MODE  = 15  /* batched launches only: 0 (default) one
+                                persistent launch over all problems; 1 one
+                                single-problem launch per problem (shared-
+                                memory mask slab and tallies), still one
+                                graph replay per run                      */
 };
 
 typedef struct sp_mc sp_mc_t;   /* opaque, owned by the library */
@@ -238,7 +243,8 @@ typedef struct sp_mc_batch sp_mc_batch_t;
 sp_mc_batch_t *sp_mc_batch_create(int n, const uint8_t *const *masks, const int *dims,
                                   const double *optics);
 /* SP_OPT_THREADS (threads per CTA, default 128), SP_OPT_BLOCKS (CTAs per SM,
- * 0 = as many as fit), SP_OPT_COMPACT, SP_OPT_GRAPH apply to the launch; the
+ * 0 = as many as fit), SP_OPT_COMPACT, SP_OPT_GRAPH and SP_OPT_BATCH_MODE
+ * apply to the launch (in mode 1 every problem uses its own launch options); the
  * path-cap, roulette and iteration-limit options apply to every problem;
  * tally mode, precision, records and photon-id offset are fixed (field,
  * FP32, none, 0). */
@@ -257,8 +263,9 @@ int sp_mc_batch_raw_field(sp_mc_batch_t *b, int i, uint64_t *dst, int on_device,
 int sp_mc_batch_reset(sp_mc_batch_t *b, void *stream);
 /* Autotuner: times one batched run of n_photons[] for each candidate launch
  * shape (threads per CTA 64/128/256, all or half the resident CTAs per SM,
- * compaction threshold 4/8/12/16), keeps the fastest, stores its rate in
- * *photons_per_s (may be NULL), then resets the tallies. */
+ * compaction threshold 4/8/12/16) and for the per-problem mode, keeps the
+ * fastest, stores its rate in *photons_per_s (may be NULL), then resets the
+ * tallies. */
 int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed,
                          double *photons_per_s, void *stream);
 void sp_mc_batch_destroy(sp_mc_batch_t *b);

@@ -599,14 +599,10 @@ int sp_mc_get_option(const sp_mc_t *h, int key, double *value) {
     }
 }
 
-int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
-    if (check_handle(h)) return SP_EINVAL;
-    if (n_photons == 0) return SP_OK;
-    if (h->pid_offset + h->photons_done + n_photons < h->pid_offset + h->photons_done)
-        return fail(SP_EINVAL, "photon id overflow");
-    DeviceGuard guard(h->device);
-    if (!guard.ok) return fail(SP_ECUDA, "cannot select device %d", h->device);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+// One single-problem transport launch of n_photons from photon id pid_begin
+// (or from *pid_begin_dev when it is set), stream-ordered and capturable.
+static int launch_run(sp_mc *h, u64 n_photons, u64 seed, u64 pid_begin, const u64 *pid_begin_dev,
+                      cudaStream_t s) {
 
     const u64 n_bricks = (u64)h->nbx * h->nby * h->nbz;
     int smem_bricks = h->smem_bricks_opt;
@@ -616,14 +612,14 @@ int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
     const bool f64 = h->precision == 64;
     const bool field = h->field != 0;
     if (smem > 48 * 1024) {
-        CUDA_TRY(cudaFuncSetAttribute(f64 ? kernel_f64(field) : kernel_f32(field),
+        CUDA_TRY(cudaFuncSetAttribute(f64 ? kernel_f64(field, h->mirror != 0) : kernel_f32(field, h->mirror != 0),
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     int blocks = h->blocks_opt;
     if (blocks <= 0) {
         int per_sm = 0;
-        CUDA_TRY(f64 ? occupancy_f64(field, h->threads, smem, &per_sm)
-                     : occupancy_f32(field, h->threads, smem, &per_sm));
+        CUDA_TRY(f64 ? occupancy_f64(field, h->mirror != 0, h->threads, smem, &per_sm)
+                     : occupancy_f32(field, h->mirror != 0, h->threads, smem, &per_sm));
         if (per_sm < 1) return fail(SP_ECUDA, "transport kernel cannot be resident with %zu B smem", smem);
         blocks = per_sm * h->sm_count;
     }
@@ -641,7 +637,8 @@ int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
     p.smem_bricks = smem_bricks;
     p.key0 = (u32)seed;
     p.key1 = (u32)(seed >> 32);
-    p.pid_begin = h->pid_offset + h->photons_done;
+    p.pid_begin = pid_begin;
+    p.pid_begin_dev = pid_begin_dev;
     p.rec_base = h->pid_offset;
     p.n_photons = n_photons;
     p.mus = h->mus; p.mua = h->mua; p.g = h->g;
@@ -656,6 +653,19 @@ int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
     CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
     CUDA_TRY(f64 ? launch_transport_f64(p, field, blocks, h->threads, smem, s)
                  : launch_transport_f32(p, field, blocks, h->threads, smem, s));
+    return SP_OK;
+}
+
+int sp_mc_run(sp_mc_t *h, uint64_t n_photons, uint64_t seed, void *stream) {
+    if (check_handle(h)) return SP_EINVAL;
+    if (n_photons == 0) return SP_OK;
+    if (h->pid_offset + h->photons_done + n_photons < h->pid_offset + h->photons_done)
+        return fail(SP_EINVAL, "photon id overflow");
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(SP_ECUDA, "cannot select device %d", h->device);
+    const int rc = launch_run(h, n_photons, seed, h->pid_offset + h->photons_done, nullptr,
+                              reinterpret_cast<cudaStream_t>(stream));
+    if (rc) return rc;
     h->photons_done += n_photons;
     return SP_OK;
 }
@@ -931,7 +941,7 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     tmp.mus = mu_s * voxel_h; tmp.mua = mu_a * voxel_h; tmp.g = g;
     tmp.porosity = porosity;
     int per_sm = 0;
-    if (occupancy_f32(false, tmp.threads, 0, &per_sm) != cudaSuccess || per_sm < 1)
+    if (occupancy_f32(false, false, tmp.threads, 0, &per_sm) != cudaSuccess || per_sm < 1)
         return fail(SP_ECUDA, "CUDA error");
 
     TransportParams p{};
@@ -1011,18 +1021,28 @@ struct sp_mc_batch {
     std::vector<BatchProblem> table;
     BatchProblem *d_table = nullptr;
     u64 *d_next = nullptr;
-    int threads = 128, blocks_per_sm = 0, compact_k = 8, use_graph = 1;
+    int threads = 128, blocks_per_sm = 0, compact_k = 8, use_graph = 1, mode = 0;
     bool table_valid = false;              // device table matches table[]
     std::vector<u64> cfg_n;                // configuration of the device table / graph
     u64 cfg_seed = 0;
     cudaStream_t cap = nullptr;            // private stream for graph capture
     cudaGraphExec_t exec = nullptr;
-    int graph_threads = 0, graph_blocks = 0, graph_compact = 0;
+    int graph_threads = 0, graph_blocks = 0, graph_compact = 0, graph_mode = 0;
+    // per-problem mode: launches fork over side streams so one problem's tail
+    // overlaps the next problem's start (graph branches when captured)
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
 };
 
 static void batch_free(sp_mc_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < sp_mc_batch::kSide; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->d_table);
     cudaFree(b->d_next);
     for (sp_mc *x : b->h) {
@@ -1088,6 +1108,9 @@ extern "C" int sp_mc_batch_set_option(sp_mc_batch_t *b, int key, double value) {
         b->compact_k = (int)value; return SP_OK;
     case SP_OPT_GRAPH:
         b->use_graph = value != 0; return SP_OK;
+    case SP_OPT_BATCH_MODE:
+        if (value != 0 && value != 1) return fail(SP_EINVAL, "batch mode must be 0 or 1");
+        b->mode = (int)value; return SP_OK;
     default: {
         // optics-independent per-problem options apply to every problem
         if (key == SP_OPT_TALLY_FIELD || key == SP_OPT_PRECISION || key == SP_OPT_RECORDS ||
@@ -1110,11 +1133,44 @@ extern "C" int sp_mc_batch_get_option(const sp_mc_batch_t *b, int key, double *v
     case SP_OPT_BLOCKS: *value = b->blocks_per_sm; return SP_OK;
     case SP_OPT_COMPACT: *value = b->compact_k; return SP_OK;
     case SP_OPT_GRAPH: *value = b->use_graph; return SP_OK;
+    case SP_OPT_BATCH_MODE: *value = b->mode; return SP_OK;
     default: return sp_mc_get_option(b->h[0], key, value);
     }
 }
 
+// Side streams and events of the per-problem mode, made before any capture.
+static int ensure_side(sp_mc_batch *b) {
+    if (b->fork) return SP_OK;
+    CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    for (int k = 0; k < sp_mc_batch::kSide; ++k) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+    }
+    return SP_OK;
+}
+
 static int batch_launch(sp_mc_batch *b, u64 total, cudaStream_t s) {
+    if (b->mode == 1) {
+        // one single-problem launch per problem; photon ids come from the
+        // device table, which the advance kernel moves on after each run
+        if (!b->fork) return fail(SP_ECUDA, "side streams not created");
+        CUDA_TRY(cudaEventRecord(b->fork, s));
+        for (int k = 0; k < sp_mc_batch::kSide; ++k) CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+        for (int i = 0, j = 0; i < b->n; ++i) {
+            if (b->cfg_n[i] == 0) continue;
+            const int rc = launch_run(b->h[i], b->cfg_n[i], b->cfg_seed, 0, &b->d_table[i].pid_begin,
+                                      b->side[j++ % sp_mc_batch::kSide]);
+            if (rc) return rc;
+        }
+        for (int k = 0; k < sp_mc_batch::kSide; ++k) {
+            CUDA_TRY(cudaEventRecord(b->join[k], b->side[k]));
+            CUDA_TRY(cudaStreamWaitEvent(s, b->join[k], 0));
+        }
+        batch_advance_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_table, b->n);
+        CUDA_TRY(cudaGetLastError());
+        b->graph_mode = 1;
+        return SP_OK;
+    }
     int per_sm = 0;
     CUDA_TRY(occupancy_batch(b->threads, &per_sm));
     if (per_sm < 1) return fail(SP_ECUDA, "batched transport cannot be resident with %d threads", b->threads);
@@ -1134,6 +1190,7 @@ static int batch_launch(sp_mc_batch *b, u64 total, cudaStream_t s) {
     b->graph_threads = b->threads;
     b->graph_blocks = per_sm;
     b->graph_compact = b->compact_k;
+    b->graph_mode = 0;
     return SP_OK;
 }
 
@@ -1145,6 +1202,10 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
     u64 total = 0;
     for (int i = 0; i < b->n; ++i) total += n_photons[i];
     if (total == 0) return SP_OK;
+    if (b->mode == 1) {
+        const int rc = ensure_side(b);
+        if (rc) return rc;
+    }
     const std::vector<u64> want(n_photons, n_photons + b->n);
     const bool same_cfg = b->table_valid && want == b->cfg_n && seed == b->cfg_seed;
     if (!same_cfg) {
@@ -1181,8 +1242,9 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
         int per_sm = 0;
         CUDA_TRY(occupancy_batch(b->threads, &per_sm));
         if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
-        if (b->exec && (b->graph_threads != b->threads || b->graph_blocks != per_sm ||
-                        b->graph_compact != b->compact_k)) {
+        if (b->exec && (b->graph_mode != b->mode ||
+                        (b->mode == 0 && (b->graph_threads != b->threads || b->graph_blocks != per_sm ||
+                                          b->graph_compact != b->compact_k)))) {
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
         }
@@ -1245,7 +1307,8 @@ extern "C" int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons,
     const int threads_c[] = {64, 128, 256};
     const int compact_c[] = {4, 8, 12, 16};
     double best = -1.0;
-    int best_t = b->threads, best_b = b->blocks_per_sm, best_k = b->compact_k;
+    int best_t = b->threads, best_b = b->blocks_per_sm, best_k = b->compact_k, best_mode = 0;
+    b->mode = 0;
     int rc = SP_OK;
     for (int t : threads_c) {
         int per_sm = 0;
@@ -1268,12 +1331,27 @@ extern "C" int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons,
             }
         }
     }
+    {   // the per-problem mode (each problem's own launch shape)
+        b->mode = 1;
+        cudaEventRecord(e0, s);
+        if ((rc = sp_mc_batch_run(b, n_photons, seed, stream)) != SP_OK) goto done;
+        cudaEventRecord(e1, s);
+        float ms = 0;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = fail(SP_ECUDA, "autotune timing failed");
+            goto done;
+        }
+        const double rate = (double)total / (ms * 1e-3);
+        if (rate > best) { best = rate; best_mode = 1; }
+        b->mode = 0;
+    }
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->threads = best_t;
     b->blocks_per_sm = best_b;
     b->compact_k = best_k;
+    b->mode = best_mode;
     b->use_graph = saved_graph;
     if (rc) return rc;
     if (photons_per_s) *photons_per_s = best;

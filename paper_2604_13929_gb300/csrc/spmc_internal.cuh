@@ -53,6 +53,7 @@ struct TransportParams {
     int smem_bricks;               // leading bricks (z-major) staged per CTA
     u32 key0, key1;                // Philox key = seed
     u64 pid_begin, n_photons;
+    const u64 *pid_begin_dev;      // if set, the first photon id is read here (graph replays)
     double mus, mua, g;
     double s_max, rr_weight, rr_mult;
     u64 iter_limit;
@@ -98,11 +99,11 @@ cudaError_t launch_transport_f32(const TransportParams &p, bool field, int block
                                  size_t smem, cudaStream_t s);
 cudaError_t launch_transport_f64(const TransportParams &p, bool field, int blocks, int threads,
                                  size_t smem, cudaStream_t s);
-cudaError_t occupancy_f32(bool field, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_f32(bool field, bool mirror, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_transport_batch(const BatchParams &b, int blocks, int threads, cudaStream_t s);
 cudaError_t occupancy_batch(int threads, int *blocks_per_sm);
-cudaError_t occupancy_f64(bool field, int threads, size_t smem, int *blocks_per_sm);
-const void *kernel_f32(bool field);
-const void *kernel_f64(bool field);
+cudaError_t occupancy_f64(bool field, bool mirror, int threads, size_t smem, int *blocks_per_sm);
+const void *kernel_f32(bool field, bool mirror);
+const void *kernel_f64(bool field, bool mirror);
 
 }  // namespace spmc

@@ -168,9 +168,13 @@ enum { M_STEP = 0, M_EVENT = 1, M_NEW = 2, M_DONE = 3 };
 // pointers when it claims a photon, so one warp can carry photons of
 // different problems; per-photon tallies go straight to the problem's global
 // integer tallies.
-template <typename Real, bool kField, bool kBatch>
-__global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const TransportParams p,
-                                                                          const BatchParams bp) {
+// Batched launches carry per-lane problem constants; three resident CTAs of
+// 256 threads need <= 85 registers, which the bound below asks for.  kMirror
+// compiles the specular lateral faces in (per lane in batched launches);
+// without it the periodic kernel carries no mirror code.
+template <typename Real, bool kField, bool kBatch, bool kMirror>
+__global__ void __launch_bounds__(256, kBatch ? 3 : SPMC_MIN_BLOCKS) transport_kernel(const TransportParams p,
+                                                                                      const BatchParams bp) {
     using O = Ops<Real>;
     constexpr bool kExact = sizeof(Real) == 8;
     extern __shared__ u64 s_bricks[];
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
     DevTallies *tal_ptr = p.tal;
     const u32 key0 = kBatch ? bp.key0 : p.key0, key1 = kBatch ? bp.key1 : p.key1;
     int prob = 0;
-    bool mirror = p.mirror != 0;                 // per lane in batched launches
+    bool mirror = kMirror && p.mirror != 0;      // per lane in batched launches
     Real mus, mua, inv_mus, inv_mua, one_m_g2, one_p_g2, one_m_g, two_g, inv_2g, g;
     Real s_max, rr_w, rr_m, rr_p, rr_gain, hist_scale;
     if constexpr (kExact) {
@@ -221,6 +225,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
     const Real kInf = O::inf();
     u32 iter_limit = p.iter_limit > 0xffffffffull ? 0xffffffffu : (u32)p.iter_limit;
     const int ck = kBatch ? bp.compact_k : p.compact_k;
+    const u64 pid0 = (!kBatch && p.pid_begin_dev) ? *p.pid_begin_dev : p.pid_begin;
     const int compact_k = ck < 1 ? 1 : (ck > 32 ? 32 : ck);
 
     // photon state
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
         const int wx = (nix >= nx) - (nix < 0), wy = (niy >= ny) - (niy < 0);
         // mirror lateral faces: at the domain edge the photon stays in its
         // voxel and the crossing component of its direction reverses
-        const bool rx = mirror && wx != 0, ry = mirror && wy != 0;
+        const bool rx = kMirror && mirror && wx != 0, ry = kMirror && mirror && wy != 0;
         nix = rx ? ix : (wx > 0 ? 0 : (wx < 0 ? nx - 1 : nix));
         niy = ry ? iy : (wy > 0 ? 0 : (wy < 0 ? ny - 1 : niy));
         const bool leaves = niz < 0 || niz >= nz;
@@ -468,7 +473,7 @@ __global__ void __launch_bounds__(256, SPMC_MIN_BLOCKS) transport_kernel(const T
                             iter_limit = pr.iter_limit;
                             mirror = pr.mirror != 0;
                         } else {
-                            pid = p.pid_begin + k;
+                            pid = pid0 + k;
                         }
                         event = 0;
                         mode = M_EVENT;
@@ -652,23 +657,29 @@ template <typename Real>
 cudaError_t launch_transport(const TransportParams &p, bool field, int blocks, int threads,
                              size_t smem, cudaStream_t s) {
     const BatchParams none{};
-    if (field) transport_kernel<Real, true, false><<<blocks, threads, smem, s>>>(p, none);
-    else transport_kernel<Real, false, false><<<blocks, threads, smem, s>>>(p, none);
+    if (p.mirror) {
+        if (field) transport_kernel<Real, true, false, true><<<blocks, threads, smem, s>>>(p, none);
+        else transport_kernel<Real, false, false, true><<<blocks, threads, smem, s>>>(p, none);
+    } else {
+        if (field) transport_kernel<Real, true, false, false><<<blocks, threads, smem, s>>>(p, none);
+        else transport_kernel<Real, false, false, false><<<blocks, threads, smem, s>>>(p, none);
+    }
     return cudaGetLastError();
 }
 
 template <typename Real>
-const void *kernel_ptr(bool field) {
-    return field ? reinterpret_cast<const void *>(&transport_kernel<Real, true, false>)
-                 : reinterpret_cast<const void *>(&transport_kernel<Real, false, false>);
+const void *kernel_ptr(bool field, bool mirror) {
+    if (mirror)
+        return field ? reinterpret_cast<const void *>(&transport_kernel<Real, true, false, true>)
+                     : reinterpret_cast<const void *>(&transport_kernel<Real, false, false, true>);
+    return field ? reinterpret_cast<const void *>(&transport_kernel<Real, true, false, false>)
+                 : reinterpret_cast<const void *>(&transport_kernel<Real, false, false, false>);
 }
 
 template <typename Real>
-cudaError_t occupancy(bool field, int threads, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm,
-        field ? transport_kernel<Real, true, false> : transport_kernel<Real, false, false>,
-        threads, smem);
+cudaError_t occupancy(bool field, bool mirror, int threads, size_t smem, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_ptr<Real>(field, mirror), threads,
+                                                         smem);
 }
 
 }  // namespace spmc

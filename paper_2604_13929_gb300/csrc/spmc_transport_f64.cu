@@ -8,10 +8,10 @@ cudaError_t launch_transport_f64(const TransportParams &p, bool field, int block
     return launch_transport<double>(p, field, blocks, threads, smem, s);
 }
 
-cudaError_t occupancy_f64(bool field, int threads, size_t smem, int *blocks_per_sm) {
-    return occupancy<double>(field, threads, smem, blocks_per_sm);
+cudaError_t occupancy_f64(bool field, bool mirror, int threads, size_t smem, int *blocks_per_sm) {
+    return occupancy<double>(field, mirror, threads, smem, blocks_per_sm);
 }
 
-const void *kernel_f64(bool field) { return kernel_ptr<double>(field); }
+const void *kernel_f64(bool field, bool mirror) { return kernel_ptr<double>(field, mirror); }
 
 }  // namespace spmc

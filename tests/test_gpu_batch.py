@@ -55,19 +55,20 @@ def _assert_same(a, af, b, bf):
     assert np.array_equal(af, bf)
 
 
-@pytest.mark.parametrize("graph", [0, 1])
-def test_batch_equals_separate_runs(spmc, problems, graph):
+@pytest.mark.parametrize("graph,mode", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_batch_equals_separate_runs(spmc, problems, graph, mode):
     n = [20000, 15000, 0, 25000]
-    with spmc.Batch(problems, graph=graph) as b:
+    with spmc.Batch(problems, graph=graph, batch_mode=mode) as b:
         b.run(n, 77)
         for i, pr in enumerate(problems):
             ref, rf = _single(spmc, pr, n[i], 77)
             _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
 
 
-def test_graph_replays_continue_photon_ids(spmc, problems):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_replays_continue_photon_ids(spmc, problems, mode):
     n = [8000, 6000, 4000, 9000]
-    with spmc.Batch(problems, graph=1) as b:
+    with spmc.Batch(problems, graph=1, batch_mode=mode) as b:
         for _ in range(3):
             b.run(n, 5)
         for i, pr in enumerate(problems):
@@ -75,8 +76,9 @@ def test_graph_replays_continue_photon_ids(spmc, problems):
             _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
 
 
-def test_batch_with_mirror_faces_equals_separate_runs(spmc, problems):
-    with spmc.Batch(problems[:2], lateral_bc=1) as b:
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_with_mirror_faces_equals_separate_runs(spmc, problems, mode):
+    with spmc.Batch(problems[:2], lateral_bc=1, batch_mode=mode) as b:
         b.run([12000, 9000], 21)
         for i, pr in enumerate(problems[:2]):
             sim = spmc.Simulation(pr[0], pr[1], pr[2], pr[3], lateral_bc=1)
@@ -90,6 +92,7 @@ def test_autotune_picks_a_shape_and_leaves_no_tallies(spmc, problems):
         rate = b.autotune([4000] * 4, 9)
         assert rate > 0
         assert b.get_option("threads") in (64, 128, 256)
+        assert b.get_option("batch_mode") in (0, 1)
         assert 1 <= b.get_option("compact") <= 32
         assert all(b.tallies(i)["photons"] == 0 for i in range(4))
         b.run([5000] * 4, 11)
