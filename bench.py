@@ -415,6 +415,39 @@ def surrogate_bench(torch, args):
     net.close()
 
 
+def surrogate_profile(torch, args):
+    """Profiling case: the c0 = 32 U-Net at 64^3, one warm-up forward+backward
+    (skipped with --surrogate-profile-cold), then one forward+backward at
+    batch B on random masks and optics; prints the milliseconds."""
+    from paper_2604_13929_gb300 import spnn
+    c0, n, B = 32, 64, args.surrogate_profile
+    net = spnn.UNet(c0, n, B)
+    net.set_params(spnn.init_params(c0, 7))
+    rng = np.random.default_rng(5)
+    mask = torch.from_numpy((rng.random((B, n, n, n)) < 0.8).astype(np.uint8)).cuda()
+    optics = torch.tensor(np.tile([[0.5, 0.005, 0.7]], (B, 1)), dtype=torch.float32).cuda()
+    x = spnn.planes_empty(B, n, n, n, 16)
+    spnn.spnn_pack_input(mask, optics, x)
+    pred = torch.empty((B, n, n, n), dtype=torch.float32, device="cuda")
+    target = torch.zeros_like(pred)
+
+    def step():
+        net.forward(x, pred)
+        net.backward(target)
+
+    if not args.surrogate_profile_cold:
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step()
+    e1.record()
+    torch.cuda.synchronize()
+    spnn.spnn_status()
+    print(json.dumps({"surrogate_profile_batch": B, "ms": e0.elapsed_time(e1)}), flush=True)
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +467,10 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--surrogate-batch", type=int, default=256)
     ap.add_argument("--surrogate-photons", type=int, default=10_000_000)
+    ap.add_argument("--surrogate-profile", type=int, default=0, metavar="B",
+                    help="profiling case: one surrogate forward+backward at batch B (64^3, c0 32)")
+    ap.add_argument("--surrogate-profile-cold", action="store_true",
+                    help="with --surrogate-profile: no warm-up step")
     ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
                     help="profiling case: one warm-up launch of N/10 photons, then one timed "
                          "launch of N photons on the workload; prints its time and exits")
@@ -473,7 +510,10 @@ def main():
         return
     if args.workload == "surrogate":
         if rank == 0:
-            surrogate_bench(torch, args)
+            if args.surrogate_profile:
+                surrogate_profile(torch, args)
+            else:
+                surrogate_bench(torch, args)
         return
     mask = make_mask("cuda")
     stream = torch.cuda.current_stream()
