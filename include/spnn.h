@@ -58,6 +58,19 @@ int spnn_version(void);
  */
 int spnn_status(void* stream);
 
+/*
+ * Launch tuning of the GEMM kernels, process-wide (0 = automatic):
+ *   SPNN_OPT_CONV_SUBTILES  128-row subtiles per CTA of a conv3 GEMM (1, 2, 4),
+ *                           stacked along y, sharing one halo box and weight copy
+ *   SPNN_OPT_CONV_PLANES    8-channel chunk planes per conv3 K-step (2, 4)
+ *   SPNN_OPT_STAGE_KB       shared-memory budget of the stage ring in KB (<= 220)
+ * Settings that do not fit a layer fall back to the automatic choice.
+ */
+#define SPNN_OPT_CONV_SUBTILES 1
+#define SPNN_OPT_CONV_PLANES 2
+#define SPNN_OPT_STAGE_KB 3
+int spnn_set_option(int key, int value);
+
 /* Elements (BF16) of a packed weight operand for a layer. */
 size_t spnn_packed_elems(int kind, int cin, int cout);
 /* FP32 w[taps][cin][cout] (device) -> packed BF16 operand (device, spnn_packed_elems). */

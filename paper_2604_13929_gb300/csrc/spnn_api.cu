@@ -153,14 +153,49 @@ void rows_geometry(RowsParams& p) {
     p.stage_bytes = (p.a_stage_bytes + p.b_stage_bytes + 1023u) & ~1023u;
 }
 
-// Planes per conv3 K-step: 4 when both concatenated sources divide by 4 and
-// the stage (A boxes + nine taps of B) stays within 56 KB, else 2.
-int conv_planes(int kc0, int kc1, const TileGrid& g, int n_total, bool halo) {
-    if (kc0 % 4 || kc1 % 4) return 2;
+// Launch tuning (spnn_set_option): conv3 subtiles per CTA, chunk planes per
+// K-step, and the shared-memory budget of the stage ring; 0 = automatic.
+int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0;
+
+int stage_budget() { return (g_opt_stage_kb > 0 ? g_opt_stage_kb : 110) * 1024; }
+
+// conv3 tiling: mt 128-row subtiles per CTA (stacked along y, sharing one halo
+// box and one weight copy) and E chunk planes per K-step.  Prefers the most
+// subtiles, then the most planes, whose stage fits half the ring budget.
+// Returns false if the grid does not tile.
+bool conv_tiling_with(int opt_mt, int opt_planes, int B, int D, int H, int W, int kc0, int kc1, int n_total,
+                      TileGrid* g, int* mt, int* E, bool* halo);
+
+bool conv_tiling(int B, int D, int H, int W, int kc0, int kc1, int n_total, TileGrid* g, int* mt, int* E,
+                 bool* halo) {
+    // options that do not fit this layer fall back to the automatic choice
+    return conv_tiling_with(g_opt_mt, g_opt_planes, B, D, H, W, kc0, kc1, n_total, g, mt, E, halo) ||
+           conv_tiling_with(0, 0, B, D, H, W, kc0, kc1, n_total, g, mt, E, halo);
+}
+
+bool conv_tiling_with(int opt_mt, int opt_planes, int B, int D, int H, int W, int kc0, int kc1, int n_total,
+                      TileGrid* g, int* mt, int* E, bool* halo) {
     const long long n_tile = n_total <= 256 ? n_total : 256;
-    const long long a = halo ? 4LL * g.bx * (g.by + 2) * 3 * 16 : 9LL * 4 * 2048;
-    const long long b = 9LL * 4 * n_tile * 16;
-    return a + b <= 56 * 1024 ? 4 : 2;
+    const int mts[3] = {4, 2, 1};
+    for (int mi = 0; mi < 3; ++mi) {
+        const int m = mts[mi];
+        if (opt_mt > 0 && m != opt_mt) continue;
+        TileGrid t;
+        if (!make_grid(kRows * m, B, D, H, W, &t)) continue;
+        const bool h = t.bz == 1 && t.bb == 1;
+        if (m > 1 && !h) continue;
+        if (m * n_tile > 512) continue;
+        for (int e : {4, 2}) {
+            if (opt_planes > 0 && e != opt_planes) continue;
+            if (kc0 % e || kc1 % e) continue;
+            const long long a = h ? (long long)e * t.bx * (t.by + 2) * 3 * 16 : 9LL * e * 2048;
+            const long long b = 9LL * e * n_tile * 16;
+            if (2 * (a + b) > stage_budget() && !(m == 1 && e == 2)) continue;
+            *g = t, *mt = m, *E = e, *halo = h;
+            return true;
+        }
+    }
+    return false;
 }
 
 // Chunk planes per K-step for the other modes: the largest even divisor of kc_total up to 8.
@@ -175,8 +210,9 @@ int rows_gemm(RowsParams& p, cudaStream_t st) {
     if (p.n_total > 256 && p.n_total % 256) return fail(SPNN_EINVAL, "GEMM N %d > 256 not a multiple of 256", p.n_total);
     if (p.kc_total < 2 || p.kc_total % 2) return fail(SPNN_EINVAL, "input channels not a multiple of 16");
     rows_geometry(p);
-    int S = (int)((110u * 1024u) / p.stage_bytes);
+    int S = (int)((uint32_t)stage_budget() / p.stage_bytes);
     p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
+    if (p.mt < 1) p.mt = 1;
     // K-major no-swizzle operands: leading-dimension offset = step between
     // 16-byte chunk planes along K, stride-dimension offset = step between
     // 8-row groups (128 bytes); the kernel builds the descriptors.
@@ -344,14 +380,19 @@ int layer_forward(int kind, int B, int D, int H, int W, const void* x0, int c0, 
     RowsParams p;
     memset(&p, 0, sizeof p);
     const int s = kind == KIND_DOWN ? 2 : 1;
-    if (!make_grid(kRows, B, D / s, H / s, W / s, &p.g)) return bad_grid(kRows, p.g);
+    p.mt = 1;
+    if (kind == KIND_CONV3) {
+        bool halo = false;
+        if (!conv_tiling(B, D, H, W, c0 / 8, c1 / 8, cout, &p.g, &p.mt, &p.E, &halo)) return bad_grid(kRows, p.g);
+        p.halo = halo;
+    } else if (!make_grid(kRows, B, D / s, H / s, W / s, &p.g)) {
+        return bad_grid(kRows, p.g);
+    }
     p.kc_total = (c0 + c1) / 8;
     p.kc0 = c0 / 8;
     if (kind == KIND_CONV3) {
         p.tap_mode = TAP_SHIFT3;
         p.n_taps = 27;
-        p.halo = p.g.bz == 1 && p.g.bb == 1;
-        p.E = conv_planes(c0 / 8, c1 / 8, p.g, cout, p.halo);
         if ((rc = map_planes(&p.maps[0], x0, c0, p.g, p.E, p.halo))) return rc;
         if (c1 && (rc = map_planes(&p.maps[1], x1, c1, p.g, p.E, p.halo))) return rc;
     } else if (kind == KIND_DOWN) {
@@ -393,10 +434,12 @@ int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, 
     const long long in_vox = (long long)B * D * H * W;
     p.kc_total = cout / 8;
     p.kc0 = p.kc_total;
+    p.mt = 1;
     if (kind == KIND_CONV3) {
-        if (!make_grid(kRows, B, D, H, W, &p.g)) return bad_grid(kRows, p.g);
-        p.halo = p.g.bz == 1 && p.g.bb == 1;
-        p.E = conv_planes(p.kc_total, 0, p.g, c0 + c1, p.halo);
+        bool halo = false;
+        if (!conv_tiling(B, D, H, W, p.kc_total, 0, c0 + c1, &p.g, &p.mt, &p.E, &halo))
+            return bad_grid(kRows, p.g);
+        p.halo = halo;
         if ((rc = map_planes(&p.maps[0], dy, cout, p.g, p.E, p.halo))) return rc;
         p.tap_mode = TAP_SHIFT3;
         p.n_taps = 27;
@@ -742,6 +785,26 @@ int spnn_status(void* stream) {
         return fail(SPNN_ECUDA, "a kernel gave up on a bounded wait (flag %d)", h);
     }
     return SPNN_OK;
+}
+
+int spnn_set_option(int key, int value) {
+    if (value < 0) return fail(SPNN_EINVAL, "option values are >= 0");
+    switch (key) {
+    case SPNN_OPT_CONV_SUBTILES:
+        if (value != 0 && value != 1 && value != 2 && value != 4) return fail(SPNN_EINVAL, "subtiles: 0, 1, 2 or 4");
+        g_opt_mt = value;
+        return SPNN_OK;
+    case SPNN_OPT_CONV_PLANES:
+        if (value != 0 && value != 2 && value != 4) return fail(SPNN_EINVAL, "planes: 0, 2 or 4");
+        g_opt_planes = value;
+        return SPNN_OK;
+    case SPNN_OPT_STAGE_KB:
+        if (value > 220) return fail(SPNN_EINVAL, "stage budget above 220 KB");
+        g_opt_stage_kb = value;
+        return SPNN_OK;
+    default:
+        return fail(SPNN_EINVAL, "unknown option %d", key);
+    }
 }
 
 size_t spnn_packed_elems(int kind, int cin, int cout) {

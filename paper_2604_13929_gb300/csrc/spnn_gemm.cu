@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t done = bar0 + 16u * S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = tmem_cols(p.n_tile);
+    const uint32_t ncols = tmem_cols(p.mt * p.n_tile);   // one accumulator per subtile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -143,9 +143,13 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                                    : a0 + (uint32_t)(t9 * p.E) * 2048u;
                         const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
                         for (int i = 0; i < p.E / 2; ++i) {
-                            const uint64_t ad = smem_desc(a_tap + 2u * i * lbo_a, lbo_a, 128);
                             const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
-                            umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                            // subtile m starts 128 rows (2048 bytes) further into the halo box
+                            for (int m = 0; m < p.mt; ++m) {
+                                const uint64_t ad = smem_desc(a_tap + 2048u * m + 2u * i * lbo_a, lbo_a, 128);
+                                umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
+                                          (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                            }
                         }
                     }
                 } else {
@@ -168,12 +172,13 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
             if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
         } else {
             tc_fence_after();
+          for (int m = 0; m < p.mt; ++m) {
             int vx, vy, vz, vb;
-            const long long vox = row_voxel(p.g, x0, y0, z0, b0, r, &vx, &vy, &vz, &vb);
+            const long long vox = row_voxel(p.g, x0, y0, z0, b0, m * kRows + r, &vx, &vy, &vz, &vb);
             float head_acc = 0.f;
             for (int j = 0; j < p.n_tile / 16; ++j) {
                 uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 16), v);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * p.n_tile + j * 16), v);
                 tmem_wait_ld();
                 const int n0 = blockIdx.y * p.n_tile + j * 16;
                 const EpiDest& d = (n0 < p.split) ? p.d[0] : p.d[1];
@@ -230,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 }
             }
             if (p.head_out) p.head_out[vox] = head_acc + *p.head_b;
+          }
         }
     }
     tc_fence_before();

@@ -84,7 +84,8 @@ struct RowsParams {
     int n_taps, kc_total, kc0, kc_step, tap_mode;
     int halo, E;                    // conv3 only
     uint32_t halo_plane;            // bytes of one chunk plane of the halo box
-    TileGrid g;
+    int mt;                         // 128-row subtiles per CTA, stacked along y (halo mode), else 1
+    TileGrid g;                     // CTA boxes: 128 * mt voxels each
     int n_tile, n_total, ksteps, stages;
     uint32_t a_stage_bytes, b_stage_bytes, stage_bytes;
     uint32_t idesc;

@@ -56,6 +56,7 @@ def load():
             "spnn_last_error": (ctypes.c_char_p, []),
             "spnn_version": (_I, []),
             "spnn_status": (_I, [_P]),
+            "spnn_set_option": (_I, [_I, _I]),
             "spnn_packed_elems": (ctypes.c_size_t, [_I, _I, _I]),
             "spnn_pack_weights": (_I, [_I, _I, _I, _I, _P, _P, _P]),
             "spnn_layer_forward": (_I, [_I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _I, _P, _P, _P, _P,
@@ -135,6 +136,13 @@ def _stream(stream):
 
 def spnn_status(stream=None):
     _check(load().spnn_status(_stream(stream)))
+
+
+OPT = {"conv_subtiles": 1, "conv_planes": 2, "stage_kb": 3}
+
+
+def spnn_set_option(key, value: int):
+    _check(load().spnn_set_option(OPT.get(key, key), int(value)))
 
 
 def spnn_packed_elems(kind: int, cin: int, cout: int) -> int:
