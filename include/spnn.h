@@ -64,11 +64,14 @@ int spnn_status(void* stream);
  *                           stacked along y, sharing one halo box and weight copy
  *   SPNN_OPT_CONV_PLANES    8-channel chunk planes per conv3 K-step (2, 4)
  *   SPNN_OPT_STAGE_KB       shared-memory budget of the stage ring in KB (<= 220)
+ *   SPNN_OPT_WGRAD_HALO     1 (default): conv3 weight gradients on halo K-steps
+ *                           where they fit; 0: always the per-tap kernel
  * Settings that do not fit a layer fall back to the automatic choice.
  */
 #define SPNN_OPT_CONV_SUBTILES 1
 #define SPNN_OPT_CONV_PLANES 2
 #define SPNN_OPT_STAGE_KB 3
+#define SPNN_OPT_WGRAD_HALO 4
 int spnn_set_option(int key, int value);
 
 /* Elements (BF16) of a packed weight operand for a layer. */

@@ -155,7 +155,7 @@ void rows_geometry(RowsParams& p) {
 
 // Launch tuning (spnn_set_option): conv3 subtiles per CTA, chunk planes per
 // K-step, and the shared-memory budget of the stage ring; 0 = automatic.
-int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0;
+int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0, g_opt_wgrad_halo = 1;
 
 int stage_budget() { return (g_opt_stage_kb > 0 ? g_opt_stage_kb : 110) * 1024; }
 
@@ -475,6 +475,65 @@ int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, 
     return rows_gemm(p, st);
 }
 
+// conv3 weight gradient on halo K-steps (see WgradHaloParams).  Returns
+// SPNN_OK, or 1 when the layer does not fit the halo scheme (caller falls back).
+int wgrad_halo(int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1, const void* dy,
+               int cout, float* dw, float* db, cudaStream_t st) {
+    const int kc0 = c0 / 8, kc1 = c1 / 8, kc = kc0 + kc1;
+    const int nM = (9 * kc + 1 + 15) / 16;
+    // 16-voxel x-runs; the second source's box must land 128-byte aligned
+    // (kc0 * 2592 bytes); every accumulator tile must fit the 512 TMEM columns
+    if (W < 16 || W % 16 || (kc1 && kc0 % 4) || 3 * nM * cout > 512 || cout > 256) return 1;
+    WgradHaloParams p;
+    memset(&p, 0, sizeof p);
+    p.kc0 = kc0;
+    p.kc1 = kc1;
+    p.n = cout;
+    p.nM = nM;
+    p.dw = dw;
+    p.db = db;
+    p.g.B = B, p.g.D = D, p.g.H = H, p.g.W = W;
+    p.g.bx = 16, p.g.by = 1, p.g.bz = 1, p.g.bb = 1;
+    p.g.nx = W / 16, p.g.ny = H, p.g.nz = D;
+    int rc;
+    const cuuint64_t row = 16ull * W;
+    auto halo_map = [&](CUtensorMap* m, const void* ptr, int C) {
+        cuuint64_t dims[5] = {8ull * W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B, (cuuint64_t)(C / 8)};
+        cuuint64_t strides[4] = {row, row * H, row * H * D, row * H * D * B};
+        cuuint32_t box[5] = {8 * 18, 3, 3, 1, (cuuint32_t)(C / 8)};
+        return encode(m, ptr, dims, strides, box);
+    };
+    if ((rc = halo_map(&p.amaps[0], x0, c0))) return rc;
+    if (c1 && (rc = halo_map(&p.amaps[1], x1, c1))) return rc;
+    {
+        cuuint64_t dims[5] = {8ull * W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B, (cuuint64_t)(cout / 8)};
+        cuuint64_t strides[4] = {row, row * H, row * H * D, row * H * D * B};
+        cuuint32_t box[5] = {8 * 16, 1, 1, 1, (cuuint32_t)(cout / 8)};
+        if ((rc = encode(&p.bmap, dy, dims, strides, box))) return rc;
+    }
+    p.ksteps_total = (int)n_tiles(p.g);
+    // A region: every row a tile can read, (16 nM + 1) rows of 288 bytes
+    p.a_region = ((uint32_t)(16 * nM + 1) * 288u + 1023u) & ~1023u;
+    p.b_stage_bytes = (uint32_t)cout * 32u;
+    p.stage_bytes = (p.a_region + p.b_stage_bytes + 1023u) & ~1023u;
+    // resident CTAs per SM: TMEM columns, then the shared-memory ring
+    const int ncols = (int)tmem_cols(3 * nM * cout);
+    const int per_sm = 512 / ncols;
+    int S = (int)((uint32_t)(per_sm > 1 ? 100 : 200) * 1024u / p.stage_bytes);
+    p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
+    p.idesc = idesc_bf16(128, cout, 1, 1);
+    p.err = err_ptr();
+    if (!p.err) return fail(SPNN_ECUDA, "no device");
+    int grid = 152 * per_sm;
+    if (grid > p.ksteps_total) grid = p.ksteps_total;
+    p.ksteps_per_cta = (p.ksteps_total + grid - 1) / grid;
+    grid = (p.ksteps_total + p.ksteps_per_cta - 1) / p.ksteps_per_cta;
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
+    cudaError_t e = launch_wgrad_halo(p, grid, smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "wgrad_halo_kernel launch");
+    return SPNN_OK;
+}
+
 int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1,
                 const void* dy, int cout, float* dw, float* db, cudaStream_t st) {
     int rc;
@@ -482,6 +541,10 @@ int layer_wgrad(int kind, int B, int D, int H, int W, const void* x0, int c0, co
     if (!x0 || !dy || !dw || (c1 && !x1)) return fail(SPNN_EINVAL, "null tensor");
     if (c1 && kind != KIND_CONV3) return fail(SPNN_EINVAL, "concatenated input only for conv3");
     if (c0 % 8 || c1 % 8) return fail(SPNN_EINVAL, "source channels must be multiples of 8");
+    if (kind == KIND_CONV3 && g_opt_wgrad_halo) {
+        const int h = wgrad_halo(B, D, H, W, x0, c0, x1, c1, dy, cout, dw, db, st);
+        if (h != 1) return h;
+    }
     WgradParams p;
     memset(&p, 0, sizeof p);
     p.mode = kind;
@@ -801,6 +864,9 @@ int spnn_set_option(int key, int value) {
     case SPNN_OPT_STAGE_KB:
         if (value > 220) return fail(SPNN_EINVAL, "stage budget above 220 KB");
         g_opt_stage_kb = value;
+        return SPNN_OK;
+    case SPNN_OPT_WGRAD_HALO:
+        g_opt_wgrad_halo = value != 0;
         return SPNN_OK;
     default:
         return fail(SPNN_EINVAL, "unknown option %d", key);

@@ -442,3 +442,146 @@ cudaError_t launch_wgrad(const WgradParams& p, dim3 grid, size_t smem, cudaStrea
 }
 
 }  // namespace spnn
+
+namespace spnn {
+
+constexpr uint32_t kHaloRow = 18 * 16;   // bytes of one halo row: 16 voxels + 2 halo, 16 B each
+
+__global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_constant__ WgradHaloParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = align1024(smem_raw);
+    const int S = p.stages;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = smem_u32(bars);
+    const uint32_t done = bar0 + 16u * S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kc = p.kc0 + p.kc1;
+    const int groups = 9 * kc;                       // real row groups; group `groups` is the ones row
+    const uint32_t ncols = tmem_cols(3 * p.nM * p.n);
+    const int kbeg = blockIdx.x * p.ksteps_per_cta;
+    const int kend = min(kbeg + p.ksteps_per_cta, p.ksteps_total);
+
+    // the ones row of every stage (written once; TMA never writes it)
+    for (int s = 0; s < S; ++s) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(smem + (size_t)s * p.stage_bytes + (size_t)groups * kHaloRow);
+        for (int i = threadIdx.x; i < (int)(kHaloRow / 4); i += blockDim.x) dst[i] = 0x3F803F80u;
+    }
+    fence_async_shared();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(bar0 + 8u * s, 1);
+            mbar_init(bar0 + 8u * (S + s), 1);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t tx = (uint32_t)kc * 9u * kHaloRow + p.b_stage_bytes;
+            for (int k = kbeg; k < kend; ++k) {
+                const int kk = k - kbeg;
+                const int s = kk % S;
+                const uint32_t r = (uint32_t)(kk / S);
+                const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
+                if (kk >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
+                    atomicOr(p.err, ERR_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(full, tx);
+                int x0, y0, z0, b0;
+                tile_origin(p.g, k, x0, y0, z0, b0);
+                const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
+                tma_load_5d(a_dst, &p.amaps[0], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, 0);
+                if (p.kc1)
+                    tma_load_5d(a_dst + (uint32_t)p.kc0 * 9u * kHaloRow, &p.amaps[1], full, 8 * (x0 - 1), y0 - 1,
+                                z0 - 1, b0, 0);
+                tma_load_5d(a_dst + p.a_region, &p.bmap, full, 8 * x0, y0, z0, b0, 0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int k = kbeg; k < kend; ++k) {
+                const int kk = k - kbeg;
+                const int s = kk % S;
+                const uint32_t r = (uint32_t)(kk / S);
+                if (!mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs)) {
+                    atomicOr(p.err, ERR_TIMEOUT);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
+                const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
+                for (int dxi = 0; dxi < 3; ++dxi)
+                    for (int j = 0; j < p.nM; ++j) {
+                        const uint64_t ad = smem_desc(a0 + 16u * dxi + (uint32_t)(16 * j) * kHaloRow, 128u, kHaloRow);
+                        umma_bf16(tmem + (uint32_t)((dxi * p.nM + j) * p.n), ad, bd, p.idesc, kk > 0 ? 1u : 0u);
+                    }
+                umma_commit(bar0 + 8u * (S + s));
+            }
+            umma_commit(done);
+        }
+    } else {
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        bool ok = mbar_wait(done, 0, kWaitLimitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+        } else if (kend > kbeg) {
+            tc_fence_after();
+            const int ci_all = 8 * kc;
+            for (int dxi = 0; dxi < 3; ++dxi)
+                for (int j = 0; j < p.nM; ++j) {
+                    const int g = 16 * j + (r >> 3), r8 = r & 7;
+                    float* dst = nullptr;
+                    if (g < groups) {
+                        const int c8 = g / 9, t9 = g % 9;   // t9 = (dz + 1) * 3 + (dy + 1)
+                        const int tap = t9 * 3 + dxi;       // (dz+1)*9 + (dy+1)*3 + (dx+1)
+                        dst = p.dw + ((size_t)tap * ci_all + c8 * 8 + r8) * p.n;
+                    } else if (g == groups && dxi == 1 && r8 == 0) {
+                        dst = p.db;
+                    }
+                    for (int c = 0; c < p.n / 16; ++c) {
+                        uint32_t v[16];
+                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((dxi * p.nM + j) * p.n + c * 16), v);
+                        tmem_wait_ld();
+                        if (dst) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) atomicAdd(dst + c * 16 + e, __uint_as_float(v[e]));
+                        }
+                    }
+                }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+cudaError_t launch_wgrad_halo(const WgradHaloParams& p, int grid, size_t smem, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(wgrad_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    wgrad_halo_kernel<<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace spnn

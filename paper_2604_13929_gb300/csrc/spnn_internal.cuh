@@ -118,7 +118,28 @@ struct WgradParams {
     int* err;
 };
 
+// conv3 weight gradient with halo K-steps: each K-step is one x-run of 16
+// output voxels; one TMA box per source brings (18 x 3 x 3) voxels of every
+// input chunk plane, laid out [plane][z][y][x] with 288-byte rows, so the
+// row groups (plane, dz, dy) sit at a uniform 288-byte stride and dx is a
+// 16-byte start offset: all 27 taps from one box.  Row group 9 * kc_total is
+// a row of ones (bias gradient, counted for dx = 0 only).  A CTA accumulates
+// 3 x nM tiles (x-shift, 16 groups) of n columns in TMEM over its K range.
+struct WgradHaloParams {
+    CUtensorMap amaps[2];           // chunk-plane maps of the sources, box (8*18, 3, 3, 1, planes)
+    CUtensorMap bmap;               // output gradient, box (8*16, 1, 1, 1, n/8)
+    int kc0, kc1, n, nM;
+    TileGrid g;                     // 16-voxel x-runs of the grid
+    int ksteps_total, ksteps_per_cta, stages;
+    uint32_t a_region, b_stage_bytes, stage_bytes;
+    uint32_t idesc;
+    float* dw;                      // [27][8 * (kc0 + kc1)][n]
+    float* db;                      // [n] or null
+    int* err;
+};
+
 cudaError_t launch_rows(const RowsParams& p, int grid_m, int grid_n, size_t smem, cudaStream_t s);
+cudaError_t launch_wgrad_halo(const WgradHaloParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_wgrad(const WgradParams& p, dim3 grid, size_t smem, cudaStream_t s);
 // TMEM columns to allocate for n FP32 accumulator columns (a power of two >= 32).
 __host__ __device__ inline uint32_t tmem_cols(int n) {

@@ -389,3 +389,27 @@ def test_conv3_tilings_agree_with_oracle(S, subtiles, planes):
     g = U.conv3_dgrad(f64(y), w_bf(w))
     ga = U.conv3_dgrad(np.abs(f64(y)), np.abs(w_bf(w)))
     check(np.concatenate([f64(dx0), f64(dx1)], axis=-1), g, ga, what="dgrad")
+
+
+@pytest.mark.parametrize("c0,c1,co,halo", [(32, 0, 32, 1), (32, 32, 32, 1), (16, 0, 32, 1), (32, 32, 32, 0)])
+def test_conv3_wgrad_halo_kernel(S, c0, c1, co, halo):
+    """conv3 weight and bias gradients with halo K-steps (all 27 taps from one
+    box per 16-voxel row) and with the per-tap kernel, against the oracle."""
+    rng = np.random.default_rng(14)
+    B, D, H, W = 2, 4, 8, 32
+    x0 = bf(rnd(rng, (B, D, H, W, c0)))
+    x1 = bf(rnd(rng, (B, D, H, W, c1))) if c1 else None
+    dy = bf(rnd(rng, (B, D, H, W, co)))
+    xin = f64(x0) if x1 is None else np.concatenate([f64(x0), f64(x1)], axis=-1)
+    ref_w, ref_b = U.conv3_wgrad(xin, f64(dy))
+    abs_w, abs_b = U.conv3_wgrad(np.abs(xin), np.abs(f64(dy)))
+    dw = torch.zeros((27, c0 + c1, co), dtype=torch.float32, device="cuda")
+    db = torch.zeros(co, dtype=torch.float32, device="cuda")
+    try:
+        S.spnn_set_option("wgrad_halo", halo)
+        S.spnn_layer_wgrad(S.CONV3, (B, D, H, W), x0, x1, dy, dw, db)
+        S.spnn_status()
+    finally:
+        S.spnn_set_option("wgrad_halo", 1)
+    check(dw.cpu().numpy().astype(np.float64), ref_w, abs_w, out_bf16=False, what="dw")
+    check(db.cpu().numpy().astype(np.float64), ref_b, abs_b, out_bf16=False, what="db")
