@@ -66,12 +66,16 @@ int spnn_status(void* stream);
  *   SPNN_OPT_STAGE_KB       shared-memory budget of the stage ring in KB (<= 220)
  *   SPNN_OPT_WGRAD_HALO     1 (default): conv3 weight gradients on halo K-steps
  *                           where they fit; 0: always the per-tap kernel
+ *   SPNN_OPT_CONV_FULL_HALO 1: conv3 forward / input gradient on 8 x 16 tiles whose
+ *                           one box per plane block serves all 27 taps, where it
+ *                           fits; 0 (default): one box per x-shift
  * Settings that do not fit a layer fall back to the automatic choice.
  */
 #define SPNN_OPT_CONV_SUBTILES 1
 #define SPNN_OPT_CONV_PLANES 2
 #define SPNN_OPT_STAGE_KB 3
 #define SPNN_OPT_WGRAD_HALO 4
+#define SPNN_OPT_CONV_FULL_HALO 5
 int spnn_set_option(int key, int value);
 
 /* Elements (BF16) of a packed weight operand for a layer. */

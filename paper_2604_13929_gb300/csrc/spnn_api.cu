@@ -106,12 +106,13 @@ int encode(CUtensorMap* m, const void* base, const cuuint64_t dims[5], const cuu
 // Chunk-plane tensor [C/8][B][D][H][W][8] on grid g: dims (8W, H, D, B, C/8);
 // coordinates (8x, y, z, b, c8).  Default box (8 bx, by, bz, bb, planes); the
 // conv3 halo box is (8 bx, by + 2, 3, 1, planes).
-int map_planes(CUtensorMap* m, const void* p, int C, const TileGrid& g, int planes = 1, bool halo = false) {
+int map_planes(CUtensorMap* m, const void* p, int C, const TileGrid& g, int planes = 1, int halo = 0) {
     const cuuint64_t row = 16ull * g.W;
     cuuint64_t dims[5] = {8ull * g.W, (cuuint64_t)g.H, (cuuint64_t)g.D, (cuuint64_t)g.B, (cuuint64_t)(C / 8)};
     cuuint64_t strides[4] = {row, row * g.H, row * g.H * g.D, row * g.H * g.D * g.B};
     cuuint32_t box[5] = {8u * g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz, (cuuint32_t)g.bb, (cuuint32_t)planes};
     if (halo) {
+        if (halo == 2) box[0] = 8u * (g.bx + 2);   // x-halo too: all 27 taps in one box
         box[1] = g.by + 2;
         box[2] = 3;
         box[3] = 1;
@@ -139,7 +140,13 @@ int n_taps_of(int kind) { return kind == KIND_CONV3 ? 27 : 8; }
 // Choose the K-step geometry of a rows GEMM (maps already hold their boxes).
 void rows_geometry(RowsParams& p) {
     p.n_tile = p.n_total <= 256 ? p.n_total : 256;
-    if (p.tap_mode == TAP_SHIFT3) {
+    if (p.tap_mode == TAP_SHIFT3 && p.halo == 2) {
+        const uint32_t nrow = (uint32_t)p.n_tile * 16u;
+        p.halo_plane = (uint32_t)((p.g.bx + 2) * (p.g.by + 2) * 3 * 16);
+        p.a_stage_bytes = p.E * p.halo_plane;
+        p.b_stage_bytes = 27u * p.E * nrow;
+        p.ksteps = p.kc_total / p.E;
+    } else if (p.tap_mode == TAP_SHIFT3) {
         const uint32_t nrow = (uint32_t)p.n_tile * 16u;
         p.halo_plane = (uint32_t)(p.g.bx * (p.g.by + 2) * 3 * 16);
         p.a_stage_bytes = p.halo ? p.E * p.halo_plane : 9u * p.E * 2048u;
@@ -155,7 +162,7 @@ void rows_geometry(RowsParams& p) {
 
 // Launch tuning (spnn_set_option): conv3 subtiles per CTA, chunk planes per
 // K-step, and the shared-memory budget of the stage ring; 0 = automatic.
-int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0, g_opt_wgrad_halo = 1;
+int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0, g_opt_wgrad_halo = 1, g_opt_full_halo = 0;
 
 int stage_budget() { return (g_opt_stage_kb > 0 ? g_opt_stage_kb : 110) * 1024; }
 
@@ -164,17 +171,45 @@ int stage_budget() { return (g_opt_stage_kb > 0 ? g_opt_stage_kb : 110) * 1024; 
 // subtiles, then the most planes, whose stage fits half the ring budget.
 // Returns false if the grid does not tile.
 bool conv_tiling_with(int opt_mt, int opt_planes, int B, int D, int H, int W, int kc0, int kc1, int n_total,
-                      TileGrid* g, int* mt, int* E, bool* halo);
+                      TileGrid* g, int* mt, int* E, int* halo);
+
+// Full-halo tiling: CTA boxes of 8 x (16 mt) voxels in one z-plane, all 27 taps
+// from one (10, 16 mt + 2, 3) box per block of E planes.
+bool full_halo_tiling(int B, int D, int H, int W, int kc0, int kc1, int n_total, TileGrid* g, int* mt, int* E) {
+    const long long n_tile = n_total <= 256 ? n_total : 256;
+    if (W % 8 || H % 16) return false;
+    for (int m : {2, 1}) {
+        if (g_opt_mt > 0 && m != g_opt_mt) continue;
+        if (H % (16 * m) || m * n_tile > 512) continue;
+        for (int e : {4, 2}) {
+            if (g_opt_planes > 0 && e != g_opt_planes) continue;
+            if (kc0 % e || kc1 % e) continue;
+            const long long a = (long long)e * 10 * (16 * m + 2) * 3 * 16;
+            const long long b = 27LL * e * n_tile * 16;
+            if (2 * (a + b) > stage_budget()) continue;
+            g->B = B, g->D = D, g->H = H, g->W = W;
+            g->bx = 8, g->by = 16 * m, g->bz = 1, g->bb = 1;
+            g->nx = W / 8, g->ny = H / (16 * m), g->nz = D;
+            *mt = m, *E = e;
+            return true;
+        }
+    }
+    return false;
+}
 
 bool conv_tiling(int B, int D, int H, int W, int kc0, int kc1, int n_total, TileGrid* g, int* mt, int* E,
-                 bool* halo) {
+                 int* halo) {
+    if (g_opt_full_halo && full_halo_tiling(B, D, H, W, kc0, kc1, n_total, g, mt, E)) {
+        *halo = 2;
+        return true;
+    }
     // options that do not fit this layer fall back to the automatic choice
     return conv_tiling_with(g_opt_mt, g_opt_planes, B, D, H, W, kc0, kc1, n_total, g, mt, E, halo) ||
            conv_tiling_with(0, 0, B, D, H, W, kc0, kc1, n_total, g, mt, E, halo);
 }
 
 bool conv_tiling_with(int opt_mt, int opt_planes, int B, int D, int H, int W, int kc0, int kc1, int n_total,
-                      TileGrid* g, int* mt, int* E, bool* halo) {
+                      TileGrid* g, int* mt, int* E, int* halo) {
     const long long n_tile = n_total <= 256 ? n_total : 256;
     const int mts[3] = {4, 2, 1};
     for (int mi = 0; mi < 3; ++mi) {
@@ -191,7 +226,7 @@ bool conv_tiling_with(int opt_mt, int opt_planes, int B, int D, int H, int W, in
             const long long a = h ? (long long)e * t.bx * (t.by + 2) * 3 * 16 : 9LL * e * 2048;
             const long long b = 9LL * e * n_tile * 16;
             if (2 * (a + b) > stage_budget() && !(m == 1 && e == 2)) continue;
-            *g = t, *mt = m, *E = e, *halo = h;
+            *g = t, *mt = m, *E = e, *halo = h ? 1 : 0;
             return true;
         }
     }
@@ -382,7 +417,7 @@ int layer_forward(int kind, int B, int D, int H, int W, const void* x0, int c0, 
     const int s = kind == KIND_DOWN ? 2 : 1;
     p.mt = 1;
     if (kind == KIND_CONV3) {
-        bool halo = false;
+        int halo = 0;
         if (!conv_tiling(B, D, H, W, c0 / 8, c1 / 8, cout, &p.g, &p.mt, &p.E, &halo)) return bad_grid(kRows, p.g);
         p.halo = halo;
     } else if (!make_grid(kRows, B, D / s, H / s, W / s, &p.g)) {
@@ -436,7 +471,7 @@ int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, 
     p.kc0 = p.kc_total;
     p.mt = 1;
     if (kind == KIND_CONV3) {
-        bool halo = false;
+        int halo = 0;
         if (!conv_tiling(B, D, H, W, p.kc_total, 0, c0 + c1, &p.g, &p.mt, &p.E, &halo))
             return bad_grid(kRows, p.g);
         p.halo = halo;
@@ -867,6 +902,9 @@ int spnn_set_option(int key, int value) {
         return SPNN_OK;
     case SPNN_OPT_WGRAD_HALO:
         g_opt_wgrad_halo = value != 0;
+        return SPNN_OK;
+    case SPNN_OPT_CONV_FULL_HALO:
+        g_opt_full_halo = value != 0;
         return SPNN_OK;
     default:
         return fail(SPNN_EINVAL, "unknown option %d", key);

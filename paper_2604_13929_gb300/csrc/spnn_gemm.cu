@@ -92,7 +92,19 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 mbar_expect_tx(full, tx);
                 const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
                 const int tap = k / gpt, g = k % gpt;
-                if (conv) {
+                if (conv && p.halo == 2) {
+                    // full halo: one box of (bx + 2, by + 2, 3) voxels per block of E planes
+                    // holds all 27 taps; the weights of the three x-shifts follow
+                    const int kc = k * p.E;
+                    const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
+                    tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, c8);
+                    const uint32_t bsz = 9u * p.E * p.n_tile * 16u;
+                    for (int dxi = 0; dxi < 3; ++dxi) {
+                        const __nv_bfloat16* src =
+                            p.wpack + ((size_t)(blockIdx.y * 3 + dxi) * p.kc_total + kc) * 9 * p.n_tile * 8;
+                        bulk_load(a_dst + p.a_stage_bytes + bsz * dxi, src, bsz, full);
+                    }
+                } else if (conv) {
                     // tap = x-shift index, g = block of E chunk planes
                     const int dx = tap - 1, kc = g * p.E;
                     const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
@@ -135,7 +147,29 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 tc_fence_after();
                 const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
                 const uint32_t b0s = a0 + p.a_stage_bytes;
-                if (conv) {
+                if (conv && p.halo == 2) {
+                    // rows of a subtile are y-runs of bx = 8 voxels: one core-matrix group
+                    // each, (bx + 2) * 16 bytes apart in the halo box; every tap is a
+                    // start offset ((dz, dy) rows, dx * 16 bytes)
+                    const uint32_t rowb = (uint32_t)(p.g.bx + 2) * 16u;
+                    const uint32_t sub = (uint32_t)(kRows / p.g.bx) * rowb;
+                    const uint32_t bsz = 9u * p.E * nrow;
+                    for (int dxi = 0; dxi < 3; ++dxi)
+                        for (int t9 = 0; t9 < 9; ++t9) {
+                            const uint32_t a_tap =
+                                a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb + 16u * dxi;
+                            for (int i = 0; i < p.E / 2; ++i) {
+                                const uint64_t bd =
+                                    smem_desc(b0s + bsz * dxi + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
+                                for (int m = 0; m < p.mt; ++m) {
+                                    const uint64_t ad =
+                                        smem_desc(a_tap + sub * m + 2u * i * p.halo_plane, p.halo_plane, rowb);
+                                    umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
+                                              (k > 0 || dxi > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                                }
+                            }
+                        }
+                } else if (conv) {
                     const uint32_t rowb = (uint32_t)p.g.bx * 16u;
                     for (int t9 = 0; t9 < 9; ++t9) {
                         const uint32_t a_tap =

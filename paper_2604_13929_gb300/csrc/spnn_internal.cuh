@@ -82,7 +82,8 @@ struct RowsParams {
     CUtensorMap maps[8];
     const __nv_bfloat16* wpack;     // packed operand, layout per kind (see the packing kernel)
     int n_taps, kc_total, kc0, kc_step, tap_mode;
-    int halo, E;                    // conv3 only
+    int halo, E;                    // conv3 only: halo 0 per-tap boxes, 1 one box per x-shift,
+                                    // 2 one box for all 27 taps (bx = 8 tiles)
     uint32_t halo_plane;            // bytes of one chunk plane of the halo box
     int mt;                         // 128-row subtiles per CTA, stacked along y (halo mode), else 1
     TileGrid g;                     // CTA boxes: 128 * mt voxels each

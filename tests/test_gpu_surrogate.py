@@ -413,3 +413,33 @@ def test_conv3_wgrad_halo_kernel(S, c0, c1, co, halo):
         S.spnn_set_option("wgrad_halo", 1)
     check(dw.cpu().numpy().astype(np.float64), ref_w, abs_w, out_bf16=False, what="dw")
     check(db.cpu().numpy().astype(np.float64), ref_b, abs_b, out_bf16=False, what="db")
+
+
+@pytest.mark.parametrize("subtiles,planes", [(1, 2), (1, 4), (2, 2), (2, 4)])
+def test_conv3_full_halo_tiling(S, subtiles, planes):
+    """The full-halo conv3 tiling (8 x 16 tiles, one box per plane block for
+    all 27 taps) against the oracle, forward and input gradient."""
+    rng = np.random.default_rng(15)
+    B, D, H, W, c0, c1, co = 1, 4, 32, 32, 32, 32, 32
+    x0, x1 = bf(rnd(rng, (B, D, H, W, c0))), bf(rnd(rng, (B, D, H, W, c1)))
+    w = rnd(rng, (27, c0 + c1, co), 0.1)
+    b = rnd(rng, co, 0.5)
+    try:
+        S.spnn_set_option("conv_full_halo", 1)
+        S.spnn_set_option("conv_subtiles", subtiles)
+        S.spnn_set_option("conv_planes", planes)
+        S.spnn_set_option("stage_kb", 200)
+        y = zeros_act(B, D, H, W, co)
+        S.spnn_layer_forward(S.CONV3, (B, D, H, W), x0, x1, packed(S, 0, c0 + c1, co, 0, w),
+                             torch.tensor(b, dtype=torch.float32, device="cuda"), co, True, y)
+        dx0, dx1 = zeros_act(B, D, H, W, c0), zeros_act(B, D, H, W, c1)
+        S.spnn_layer_dgrad(S.CONV3, (B, D, H, W), y, packed(S, 0, c0 + c1, co, 1, w), c0, c1, dx0, dx1=dx1)
+        S.spnn_status()
+    finally:
+        for k in ("conv_full_halo", "conv_subtiles", "conv_planes", "stage_kb"):
+            S.spnn_set_option(k, 0)
+    xin = np.concatenate([f64(x0), f64(x1)], axis=-1)
+    check(f64(y), U.relu(U.conv3(xin, w_bf(w), b)), U.conv3(np.abs(xin), np.abs(w_bf(w)), np.abs(b)), what="fwd")
+    g = U.conv3_dgrad(f64(y), w_bf(w))
+    ga = U.conv3_dgrad(np.abs(f64(y)), np.abs(w_bf(w)))
+    check(np.concatenate([f64(dx0), f64(dx1)], axis=-1), g, ga, what="dgrad")
