@@ -43,7 +43,7 @@ OPS_STEP, OPS_INTERACT, OPS_LAUNCH = 30, 120, 90
 ISSUE_PER_SM_CLK = 4          # warp instructions per SM per clock (4 schedulers)
 # DRAM bytes (read + write) per photon of the transport kernel from one ncu capture
 # (2e7 photons of this workload), valid only for the kernel source it was taken on.
-TRAFFIC_CAPTURE = {"kernel_sha256_prefix": "bdec2f82e6676a00", "dram_bytes_per_photon": 16282.4,
+TRAFFIC_CAPTURE = {"kernel_sha256_prefix": "e811141632e4586f", "dram_bytes_per_photon": 16287.6,
                    "source": "profiles/transport_kernel_256cubed_phi090.md"}
 
 
