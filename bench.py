@@ -462,9 +462,9 @@ def main():
                     help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
                          "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
     ap.add_argument("--precision-photons", type=int, default=1_000_000_000)
-    ap.add_argument("--surrogate-train", type=int, default=2048)
+    ap.add_argument("--surrogate-train", type=int, default=4096)
     ap.add_argument("--surrogate-test", type=int, default=128)
-    ap.add_argument("--surrogate-steps", type=int, default=1500)
+    ap.add_argument("--surrogate-steps", type=int, default=3000)
     ap.add_argument("--surrogate-batch", type=int, default=256)
     ap.add_argument("--surrogate-photons", type=int, default=10_000_000)
     ap.add_argument("--surrogate-profile", type=int, default=0, metavar="B",
