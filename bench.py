@@ -597,7 +597,7 @@ def main():
                 "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_note": "DRAM read+write bytes per launch, ncu capture of 2e7 photons "
                                 "scaled by the photon count (null if the kernel changed since)",
-                "kernel": "spmc::transport_kernel<float,true>",
+                "kernel": "spmc::transport_kernel<float,true,false,false>",
                 "peak_source": f"{props.multi_processor_count} SMs x {ISSUE_PER_SM_CLK} "
                                f"warp-inst/clk x {max_mhz:.0f} MHz (max SM clock)",
                 "launch_ms": launch_ms,
