@@ -111,3 +111,16 @@ def test_surrogate_rejects_bad_shapes_before_device_work(nnlib):
     assert nnlib.spnn_layer_forward(0, 1, 8, 8, 8, None, 16, None, 0, None, None, 32, 1, None,
                                     None, None, None, None) == spnn.SPNN_EINVAL
     assert nnlib.spnn_layer_wgrad(1, 1, 8, 8, 8, None, 16, None, 0, None, 32, None, None, None) == spnn.SPNN_EINVAL
+
+
+def test_surrogate_options_are_validated_without_a_device(nnlib):
+    """Launch-tuning options reject values outside their sets before any device work."""
+    from paper_2604_13929_gb300 import spnn
+    assert nnlib.spnn_set_option(spnn.OPT["conv_subtiles"], 3) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_set_option(spnn.OPT["conv_planes"], 8) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_set_option(spnn.OPT["stage_kb"], 500) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_set_option(99, 1) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_set_option(spnn.OPT["conv_subtiles"], -1) == spnn.SPNN_EINVAL
+    for key in ("conv_subtiles", "conv_planes", "stage_kb", "wgrad_halo", "conv_full_halo"):
+        assert nnlib.spnn_set_option(spnn.OPT[key], 0) == spnn.SPNN_OK
+    assert nnlib.spnn_set_option(spnn.OPT["wgrad_halo"], 1) == spnn.SPNN_OK
