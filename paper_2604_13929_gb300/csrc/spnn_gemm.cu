@@ -161,52 +161,52 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                             for (int i = 0; i < p.E / 2; ++i) {
                                 const uint64_t bd =
                                     smem_desc(b0s + bsz * dxi + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
-                                  for (int m = 0; m < p.mt; ++m) {
-                                        const uint64_t ad =
-                                            smem_desc(a_tap + sub * m + 2u * i * p.halo_plane, p.halo_plane, rowb);
-                                        umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
-                                                  (k > 0 || dxi > 0 || t9 > 0 || i > 0) ? 1u : 0u);
-                                    }
-                                }
-                            }
-                    } else if (conv) {
-                        const uint32_t rowb = (uint32_t)p.g.bx * 16u;
-                        for (int t9 = 0; t9 < 9; ++t9) {
-                            const uint32_t a_tap =
-                                p.halo ? a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb
-                                       : a0 + (uint32_t)(t9 * p.E) * 2048u;
-                            const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
-                            for (int i = 0; i < p.E / 2; ++i) {
-                                const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
-                                // subtile m starts 128 rows (2048 bytes) further into the halo box
                                 for (int m = 0; m < p.mt; ++m) {
-                                    const uint64_t ad = smem_desc(a_tap + 2048u * m + 2u * i * lbo_a, lbo_a, 128);
+                                    const uint64_t ad =
+                                        smem_desc(a_tap + sub * m + 2u * i * p.halo_plane, p.halo_plane, rowb);
                                     umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
-                                              (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                                              (k > 0 || dxi > 0 || t9 > 0 || i > 0) ? 1u : 0u);
                                 }
                             }
                         }
-                    } else {
-                        for (int i = 0; i < p.kc_step / 2; ++i) {
-                            const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
-                            const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
-                            umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                } else if (conv) {
+                    const uint32_t rowb = (uint32_t)p.g.bx * 16u;
+                    for (int t9 = 0; t9 < 9; ++t9) {
+                        const uint32_t a_tap =
+                            p.halo ? a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb
+                                   : a0 + (uint32_t)(t9 * p.E) * 2048u;
+                        const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
+                        for (int i = 0; i < p.E / 2; ++i) {
+                            const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
+                            // subtile m starts 128 rows (2048 bytes) further into the halo box
+                            for (int m = 0; m < p.mt; ++m) {
+                                const uint64_t ad = smem_desc(a_tap + 2048u * m + 2u * i * lbo_a, lbo_a, 128);
+                                umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
+                                          (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                            }
                         }
                     }
-                    umma_commit(bar0 + 8u * (S + s));
+                } else {
+                    for (int i = 0; i < p.kc_step / 2; ++i) {
+                        const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
+                        const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
+                        umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                    }
                 }
-                umma_commit(done);
+                umma_commit(bar0 + 8u * (S + s));
             }
+            umma_commit(done);
+        }
+    } else {
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        bool ok = mbar_wait(done, 0, kWaitLimitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
         } else {
-            const int q = warp & 3;
-            const int r = q * 32 + lane;
-            bool ok = mbar_wait(done, 0, kWaitLimitNs);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
-            } else {
-                tc_fence_after();
-              for (int m = 0; m < p.mt; ++m) {
+            tc_fence_after();
+            for (int m = 0; m < p.mt; ++m) {
                 int vx, vy, vz, vb;
                 const long long vox = row_voxel(p.g, x0, y0, z0, b0, m * kRows + r, &vx, &vy, &vz, &vb);
                 float head_acc = 0.f;
@@ -232,36 +232,36 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                         off = (ch0 >> 3) * d.plane + vox * 8;
                     }
                     float f[16];
-    #pragma unroll
+                    #pragma unroll
                     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
                     if (d.bias) {
-    #pragma unroll
+                        #pragma unroll
                         for (int i = 0; i < 16; ++i) f[i] += d.bias[ch0 + i];
                     }
                     if (d.addend) {
                         float a[16];
                         load16_planes(d.addend + off, d.plane, a);
-    #pragma unroll
+                        #pragma unroll
                         for (int i = 0; i < 16; ++i) f[i] += a[i];
                     }
                     if (d.relu) {
-    #pragma unroll
+                        #pragma unroll
                         for (int i = 0; i < 16; ++i) f[i] = fmaxf(f[i], 0.f);
                     }
                     if (d.mask) {
                         float m[16];
                         load16_planes(d.mask + off, d.plane, m);
-    #pragma unroll
+                        #pragma unroll
                         for (int i = 0; i < 16; ++i) f[i] = (m[i] > 0.f) ? f[i] : 0.f;
                     }
                     uint4 w[2];
                     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
-    #pragma unroll
+                    #pragma unroll
                     for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
                     *reinterpret_cast<uint4*>(d.out + off) = w[0];
                     *reinterpret_cast<uint4*>(d.out + off + d.plane) = w[1];
                     if (p.head_out) {
-    #pragma unroll
+                        #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const float2 rb = __bfloat1622float2(h[i]);
                             head_acc += rb.x * p.head_w[ch0 + 2 * i] + rb.y * p.head_w[ch0 + 2 * i + 1];
