@@ -39,6 +39,46 @@ __device__ __forceinline__ void load_box(uint32_t dst, const CUtensorMap* m, uin
         tma_load_5d(dst, m, bar, 8 * x, y, z, b, c8);
 }
 
+// The MMAs of one conv3 K-step: nine (dz, dy) taps x EH K-slices of 16
+// channels x MT subtiles.  Descriptors are the step's base descriptors plus
+// start-address offsets in 16-byte units (no carry: every address is inside
+// shared memory): tap_off[t9] for the tap, a_koff per K-slice, 128 (2048
+// bytes) per subtile; B holds [slice][tap] blocks of n_tile rows.  Unrolled so
+// that one instruction stream issues every MMA back to back.
+template <int MT, int EH>
+__device__ __forceinline__ void issue_conv_step(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                                const uint32_t (&tap_off)[9], uint32_t a_koff, uint32_t n_tile,
+                                                uint32_t idesc, bool first) {
+#pragma unroll
+    for (int t9 = 0; t9 < 9; ++t9)
+#pragma unroll
+        for (int i = 0; i < EH; ++i) {
+            const uint64_t bd = bdesc + (uint64_t)((uint32_t)(2 * i * 9 + t9) * n_tile);
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const uint64_t ad = adesc + (uint64_t)(tap_off[t9] + (uint32_t)i * a_koff + 128u * m);
+                umma_bf16(tmem + (uint32_t)m * n_tile, ad, bd, idesc, (first && t9 == 0 && i == 0) ? 0u : 1u);
+            }
+        }
+}
+
+__device__ __forceinline__ void issue_conv_step(int mt, int eh, uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                                const uint32_t (&tap_off)[9], uint32_t a_koff, uint32_t n_tile,
+                                                uint32_t idesc, bool first) {
+    if (mt == 4 && eh == 2)
+        issue_conv_step<4, 2>(tmem, adesc, bdesc, tap_off, a_koff, n_tile, idesc, first);
+    else if (mt == 4)
+        issue_conv_step<4, 1>(tmem, adesc, bdesc, tap_off, a_koff, n_tile, idesc, first);
+    else if (mt == 2 && eh == 2)
+        issue_conv_step<2, 2>(tmem, adesc, bdesc, tap_off, a_koff, n_tile, idesc, first);
+    else if (mt == 2)
+        issue_conv_step<2, 1>(tmem, adesc, bdesc, tap_off, a_koff, n_tile, idesc, first);
+    else if (eh == 2)
+        issue_conv_step<1, 2>(tmem, adesc, bdesc, tap_off, a_koff, n_tile, idesc, first);
+    else
+        issue_conv_step<1, 1>(tmem, adesc, bdesc, tap_off, a_koff, n_tile, idesc, first);
+}
+
 // ------------------------------------------------------------------------
 // Rows GEMM (forward, input-gradient and transposed-conv layers).
 // A tile: kc_step chunk planes of 128 rows x 16 bytes (2 KB each), K-major;
@@ -135,19 +175,30 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            const uint32_t nrow = (uint32_t)p.n_tile * 16u;   // bytes of one packed chunk of B
-            for (int k = 0; k < p.ksteps; ++k) {
-                const int s = k % S;
-                const uint32_t r = (uint32_t)(k / S);
-                if (!mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs)) {
-                    atomicOr(p.err, ERR_TIMEOUT);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
-                const uint32_t b0s = a0 + p.a_stage_bytes;
-                if (conv && p.halo == 2) {
+        // The whole warp walks the K-steps, so the descriptor arithmetic stays
+        // warp-uniform; one elected lane issues every MMA and commit.
+        const bool leader = elect_one();
+        const uint32_t nrow = (uint32_t)p.n_tile * 16u;   // bytes of one packed chunk of B
+        // conv3 with halo 0 / 1: start offsets (16-byte units) of the nine (dz, dy)
+        // taps and the A operand's K-direction core-matrix stride
+        const uint32_t a_lbo = p.halo == 1 ? p.halo_plane : 2048u;
+        uint32_t tap_off[9];
+#pragma unroll
+        for (int t9 = 0; t9 < 9; ++t9)
+            tap_off[t9] = p.halo == 1 ? (uint32_t)(((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * p.g.bx)
+                                      : (uint32_t)(t9 * p.E) * 128u;
+        for (int k = 0; k < p.ksteps; ++k) {
+            const int s = k % S;
+            const uint32_t r = (uint32_t)(k / S);
+            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
+                if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
+            const uint32_t b0s = a0 + p.a_stage_bytes;
+            if (conv && p.halo == 2) {
+                if (leader) {
                     // rows of a subtile are y-runs of bx = 8 voxels: one core-matrix group
                     // each, (bx + 2) * 16 bytes apart in the halo box; every tap is a
                     // start offset ((dz, dy) rows, dx * 16 bytes)
@@ -169,34 +220,24 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                                 }
                             }
                         }
-                } else if (conv) {
-                    const uint32_t rowb = (uint32_t)p.g.bx * 16u;
-                    for (int t9 = 0; t9 < 9; ++t9) {
-                        const uint32_t a_tap =
-                            p.halo ? a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb
-                                   : a0 + (uint32_t)(t9 * p.E) * 2048u;
-                        const uint32_t lbo_a = p.halo ? p.halo_plane : 2048u;
-                        for (int i = 0; i < p.E / 2; ++i) {
-                            const uint64_t bd = smem_desc(b0s + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
-                            // subtile m starts 128 rows (2048 bytes) further into the halo box
-                            for (int m = 0; m < p.mt; ++m) {
-                                const uint64_t ad = smem_desc(a_tap + 2048u * m + 2u * i * lbo_a, lbo_a, 128);
-                                umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
-                                          (k > 0 || t9 > 0 || i > 0) ? 1u : 0u);
-                            }
-                        }
-                    }
-                } else {
-                    for (int i = 0; i < p.kc_step / 2; ++i) {
-                        const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
-                        const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
-                        umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
-                    }
                 }
-                umma_commit(bar0 + 8u * (S + s));
+            } else if (conv) {
+                const uint64_t ad = smem_desc(a0, a_lbo, 128), bd = smem_desc(b0s, 9u * nrow, 128);
+                if (leader)
+                    issue_conv_step(p.mt, p.E / 2, tmem, ad, bd, tap_off, a_lbo / 8u, (uint32_t)p.n_tile, p.idesc,
+                                    k == 0);
+            } else if (leader) {
+                for (int i = 0; i < p.kc_step / 2; ++i) {
+                    const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
+                    const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
+                    umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                }
             }
-            umma_commit(done);
+            if (leader) umma_commit(bar0 + 8u * (S + s));
+            __syncwarp();
         }
+        if (leader) umma_commit(done);
+        __syncwarp();
     } else {
         const int q = warp & 3;
         const int r = q * 32 + lane;
@@ -386,27 +427,30 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            for (int k = kbeg; k < kend; ++k) {
-                const int kk = k - kbeg;
-                const int s = kk % S;
-                const uint32_t r = (uint32_t)(kk / S);
-                if (!mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs)) {
-                    atomicOr(p.err, ERR_TIMEOUT);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
-                const uint32_t b0s = a0 + p.a_stage_bytes;
-                for (int i = 0; i < p.kv / 16; ++i) {
-                    const uint64_t ad = smem_desc(a0 + 256u * i, 128u, gbytes);
-                    const uint64_t bd = smem_desc(b0s + 256u * i, 128u, gbytes);
-                    umma_bf16(tmem, ad, bd, p.idesc, (kk > 0 || i > 0) ? 1u : 0u);
-                }
+        // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
+        const bool leader = elect_one();
+        for (int k = kbeg; k < kend; ++k) {
+            const int kk = k - kbeg;
+            const int s = kk % S;
+            const uint32_t r = (uint32_t)(kk / S);
+            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
+                if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
+            const uint32_t b0s = a0 + p.a_stage_bytes;
+            // K-slice i starts 256 bytes (16 units) further in both operands
+            const uint64_t ad = smem_desc(a0, 128u, gbytes), bd = smem_desc(b0s, 128u, gbytes);
+            if (leader) {
+                for (int i = 0; i < p.kv / 16; ++i)
+                    umma_bf16(tmem, ad + 16u * i, bd + 16u * i, p.idesc, (kk > 0 || i > 0) ? 1u : 0u);
                 umma_commit(bar0 + 8u * (S + s));
             }
-            umma_commit(done);
+            __syncwarp();
         }
+        if (leader) umma_commit(done);
+        __syncwarp();
     } else {
         const int q = warp & 3;
         const int r = q * 32 + lane;
@@ -544,27 +588,33 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            for (int k = kbeg; k < kend; ++k) {
-                const int kk = k - kbeg;
-                const int s = kk % S;
-                const uint32_t r = (uint32_t)(kk / S);
-                if (!mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs)) {
-                    atomicOr(p.err, ERR_TIMEOUT);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
-                const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
+        // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
+        const bool leader = elect_one();
+        for (int k = kbeg; k < kend; ++k) {
+            const int kk = k - kbeg;
+            const int s = kk % S;
+            const uint32_t r = (uint32_t)(kk / S);
+            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
+                if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
+            const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
+            // dx is a 16-byte (1 unit) start offset, row block j starts 16 rows of kHaloRow bytes further
+            const uint64_t ad = smem_desc(a0, 128u, kHaloRow);
+            if (leader) {
+#pragma unroll
                 for (int dxi = 0; dxi < 3; ++dxi)
-                    for (int j = 0; j < p.nM; ++j) {
-                        const uint64_t ad = smem_desc(a0 + 16u * dxi + (uint32_t)(16 * j) * kHaloRow, 128u, kHaloRow);
-                        umma_bf16(tmem + (uint32_t)((dxi * p.nM + j) * p.n), ad, bd, p.idesc, kk > 0 ? 1u : 0u);
-                    }
+                    for (int j = 0; j < p.nM; ++j)
+                        umma_bf16(tmem + (uint32_t)((dxi * p.nM + j) * p.n), ad + (uint32_t)(dxi + j * kHaloRow), bd,
+                                  p.idesc, kk > 0 ? 1u : 0u);
                 umma_commit(bar0 + 8u * (S + s));
             }
-            umma_commit(done);
+            __syncwarp();
         }
+        if (leader) umma_commit(done);
+        __syncwarp();
     } else {
         const int q = warp & 3;
         const int r = q * 32 + lane;
