@@ -18,6 +18,31 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
+// Stage index and wrap count of a ring of S stages, advanced once per K-step
+// (the K loops avoid integer division, which costs a lone thread hundreds of
+// cycles per step).
+struct Ring {
+    int s = 0;
+    uint32_t r = 0;
+    __device__ __forceinline__ void next(int S) {
+        if (++s == S) {
+            s = 0;
+            ++r;
+        }
+    }
+};
+
+// Origin of the tile after (x0, y0, z0, b0): the increment of tile_origin.
+__device__ __forceinline__ void tile_next(const TileGrid& g, int& x0, int& y0, int& z0, int& b0) {
+    if ((x0 += g.bx) < g.nx * g.bx) return;
+    x0 = 0;
+    if ((y0 += g.by) < g.ny * g.by) return;
+    y0 = 0;
+    if ((z0 += g.bz) < g.nz * g.bz) return;
+    z0 = 0;
+    b0 += g.bb;
+}
+
 // 16 channels of one voxel: 8 at p[0..7] and 8 one chunk plane further.
 __device__ __forceinline__ void load16_planes(const __nv_bfloat16* p, long long plane, float (&f)[16]) {
     uint4 u[2] = {*reinterpret_cast<const uint4*>(p), *reinterpret_cast<const uint4*>(p + plane)};
@@ -121,9 +146,11 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
         if (lane == 0) {
             const int gpt = conv ? p.kc_total / p.E : p.kc_total / p.kc_step;
             const uint32_t tx = p.a_stage_bytes + p.b_stage_bytes;
-            for (int k = 0; k < p.ksteps; ++k) {
-                const int s = k % S;
-                const uint32_t r = (uint32_t)(k / S);
+            Ring q;
+            int tap = 0, g = 0;   // K-step k = tap * gpt + g
+            for (int k = 0; k < p.ksteps; ++k, q.next(S), g = (g + 1 < gpt) ? g + 1 : 0, tap += (g == 0)) {
+                const int s = q.s;
+                const uint32_t r = q.r;
                 const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
                 if (k >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
                     atomicOr(p.err, ERR_TIMEOUT);
@@ -131,7 +158,6 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 }
                 mbar_expect_tx(full, tx);
                 const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-                const int tap = k / gpt, g = k % gpt;
                 if (conv && p.halo == 2) {
                     // full halo: one box of (bx + 2, by + 2, 3) voxels per block of E planes
                     // holds all 27 taps; the weights of the three x-shifts follow
@@ -187,9 +213,10 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
         for (int t9 = 0; t9 < 9; ++t9)
             tap_off[t9] = p.halo == 1 ? (uint32_t)(((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * p.g.bx)
                                       : (uint32_t)(t9 * p.E) * 128u;
-        for (int k = 0; k < p.ksteps; ++k) {
-            const int s = k % S;
-            const uint32_t r = (uint32_t)(k / S);
+        Ring q;
+        for (int k = 0; k < p.ksteps; ++k, q.next(S)) {
+            const int s = q.s;
+            const uint32_t r = q.r;
             if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
                 if (leader) atomicOr(p.err, ERR_TIMEOUT);
                 break;
@@ -375,64 +402,69 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
-            int real = 0;
-            for (int sl = 0; sl < ng; ++sl) real += (sl != ones_slot);
-            const uint32_t tx = gbytes * real + (uint32_t)(p.n / 8) * gbytes;
-            for (int k = kbeg; k < kend; ++k) {
-                const int kk = k - kbeg;
-                const int s = kk % S;
-                const uint32_t r = (uint32_t)(kk / S);
-                const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
-                if (kk >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
-                    atomicOr(p.err, ERR_TIMEOUT);
-                    break;
+        // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
+        const bool leader = elect_one();
+        int real = 0;
+        for (int sl = 0; sl < ng; ++sl) real += (sl != ones_slot);
+        const uint32_t tx = gbytes * real + (uint32_t)(p.n / 8) * gbytes;
+        Ring q;
+        int x0, y0, z0, b0;
+        tile_origin(p.g, kbeg, x0, y0, z0, b0);
+        for (int k = kbeg; k < kend; ++k, q.next(S), tile_next(p.g, x0, y0, z0, b0)) {
+            const int kk = k - kbeg;
+            const int s = q.s;
+            const uint32_t r = q.r;
+            const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
+            if (kk >= S && !__all_sync(0xffffffffu, mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs))) {
+                if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            if (leader) mbar_expect_tx(full, tx);
+            const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
+            for (int sl = 0; sl < ng;) {
+                if (sl == ones_slot) {
+                    ++sl;
+                    continue;
                 }
-                mbar_expect_tx(full, tx);
-                int x0, y0, z0, b0;
-                tile_origin(p.g, k, x0, y0, z0, b0);
-                const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-                for (int sl = 0; sl < ng;) {
-                    if (sl == ones_slot) {
-                        ++sl;
-                        continue;
+                const int g = g0 + sl;
+                int mi = 0, c8, dx = 0, dy = 0, dz = 0;
+                if (p.mode == KIND_CONV3) {
+                    const int tap = g / p.kc_total;
+                    c8 = g % p.kc_total;
+                    dz = tap / 9 - 1;
+                    dy = (tap / 3) % 3 - 1;
+                    dx = tap % 3 - 1;
+                    if (c8 >= p.kc0) {
+                        mi = 1;
+                        c8 -= p.kc0;
                     }
-                    const int g = g0 + sl;
-                    int mi = 0, c8, dx = 0, dy = 0, dz = 0;
-                    if (p.mode == KIND_CONV3) {
-                        const int tap = g / p.kc_total;
-                        c8 = g % p.kc_total;
-                        dz = tap / 9 - 1;
-                        dy = (tap / 3) % 3 - 1;
-                        dx = tap % 3 - 1;
-                        if (c8 >= p.kc0) {
-                            mi = 1;
-                            c8 -= p.kc0;
-                        }
-                    } else if (p.mode == KIND_DOWN) {
-                        mi = g / p.kc_total;
-                        c8 = g % p.kc_total;
-                    } else {
-                        c8 = g;
-                    }
-                    // one box brings ea consecutive chunk planes (runs never straddle a tap or source)
+                } else if (p.mode == KIND_DOWN) {
+                    mi = g / p.kc_total;
+                    c8 = g % p.kc_total;
+                } else {
+                    c8 = g;
+                }
+                // one box brings ea consecutive chunk planes (runs never straddle a tap or source)
+                if (leader)
                     load_box(a_dst + gbytes * sl, &p.amaps[mi], full, p.mode == KIND_DOWN, c8, x0 + dx, y0 + dy,
                              z0 + dz, b0, p.g.B);
-                    sl += p.ea;
-                }
-                const CUtensorMap* bm = &p.bmaps[p.mode == KIND_UP ? btap : 0];
-                for (int j = 0; j < p.n / 8; j += p.eb)
+                sl += p.ea;
+            }
+            const CUtensorMap* bm = &p.bmaps[p.mode == KIND_UP ? btap : 0];
+            for (int j = 0; j < p.n / 8; j += p.eb)
+                if (leader)
                     load_box(a_dst + p.a_stage_bytes + gbytes * j, bm, full, p.mode == KIND_UP, j, x0, y0, z0, b0,
                              p.g.B);
-            }
+            __syncwarp();
         }
     } else if (warp == 1) {
         // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
         const bool leader = elect_one();
-        for (int k = kbeg; k < kend; ++k) {
+        Ring q;
+        for (int k = kbeg; k < kend; ++k, q.next(S)) {
             const int kk = k - kbeg;
-            const int s = kk % S;
-            const uint32_t r = (uint32_t)(kk / S);
+            const int s = q.s;
+            const uint32_t r = q.r;
             if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
                 if (leader) atomicOr(p.err, ERR_TIMEOUT);
                 break;
@@ -565,35 +597,40 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
-            const uint32_t tx = (uint32_t)kc * 9u * kHaloRow + p.b_stage_bytes;
-            for (int k = kbeg; k < kend; ++k) {
-                const int kk = k - kbeg;
-                const int s = kk % S;
-                const uint32_t r = (uint32_t)(kk / S);
-                const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
-                if (kk >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
-                    atomicOr(p.err, ERR_TIMEOUT);
-                    break;
-                }
+        // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
+        const bool leader = elect_one();
+        const uint32_t tx = (uint32_t)kc * 9u * kHaloRow + p.b_stage_bytes;
+        Ring q;
+        int x0, y0, z0, b0;
+        tile_origin(p.g, kbeg, x0, y0, z0, b0);
+        for (int k = kbeg; k < kend; ++k, q.next(S), tile_next(p.g, x0, y0, z0, b0)) {
+            const int kk = k - kbeg;
+            const int s = q.s;
+            const uint32_t r = q.r;
+            const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
+            if (kk >= S && !__all_sync(0xffffffffu, mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs))) {
+                if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
+            if (leader) {
                 mbar_expect_tx(full, tx);
-                int x0, y0, z0, b0;
-                tile_origin(p.g, k, x0, y0, z0, b0);
-                const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
                 tma_load_5d(a_dst, &p.amaps[0], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, 0);
                 if (p.kc1)
                     tma_load_5d(a_dst + (uint32_t)p.kc0 * 9u * kHaloRow, &p.amaps[1], full, 8 * (x0 - 1), y0 - 1,
                                 z0 - 1, b0, 0);
                 tma_load_5d(a_dst + p.a_region, &p.bmap, full, 8 * x0, y0, z0, b0, 0);
             }
+            __syncwarp();
         }
     } else if (warp == 1) {
         // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
         const bool leader = elect_one();
-        for (int k = kbeg; k < kend; ++k) {
+        Ring q;
+        for (int k = kbeg; k < kend; ++k, q.next(S)) {
             const int kk = k - kbeg;
-            const int s = kk % S;
-            const uint32_t r = (uint32_t)(kk / S);
+            const int s = q.s;
+            const uint32_t r = q.r;
             if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
                 if (leader) atomicOr(p.err, ERR_TIMEOUT);
                 break;
