@@ -407,6 +407,31 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
         int real = 0;
         for (int sl = 0; sl < ng; ++sl) real += (sl != ones_slot);
         const uint32_t tx = gbytes * real + (uint32_t)(p.n / 8) * gbytes;
+        // every K-step loads the same slots: lane sl decodes slot sl once (source
+        // map mi, chunk plane c8, tap shift), packed mi | c8 << 4 | (dx, dy, dz) + 1
+        // in bits 14, 16, 18
+        int code = 0;
+        if (lane < ng && lane != ones_slot) {
+            const int g = g0 + lane;
+            int mi = 0, c8, dx = 0, dy = 0, dz = 0;
+            if (p.mode == KIND_CONV3) {
+                const int tap = g / p.kc_total;
+                c8 = g % p.kc_total;
+                dz = tap / 9 - 1;
+                dy = (tap / 3) % 3 - 1;
+                dx = tap % 3 - 1;
+                if (c8 >= p.kc0) {
+                    mi = 1;
+                    c8 -= p.kc0;
+                }
+            } else if (p.mode == KIND_DOWN) {
+                mi = g / p.kc_total;
+                c8 = g % p.kc_total;
+            } else {
+                c8 = g;
+            }
+            code = mi | (c8 << 4) | ((dx + 1) << 14) | ((dy + 1) << 16) | ((dz + 1) << 18);
+        }
         Ring q;
         int x0, y0, z0, b0;
         tile_origin(p.g, kbeg, x0, y0, z0, b0);
@@ -426,24 +451,9 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
                     ++sl;
                     continue;
                 }
-                const int g = g0 + sl;
-                int mi = 0, c8, dx = 0, dy = 0, dz = 0;
-                if (p.mode == KIND_CONV3) {
-                    const int tap = g / p.kc_total;
-                    c8 = g % p.kc_total;
-                    dz = tap / 9 - 1;
-                    dy = (tap / 3) % 3 - 1;
-                    dx = tap % 3 - 1;
-                    if (c8 >= p.kc0) {
-                        mi = 1;
-                        c8 -= p.kc0;
-                    }
-                } else if (p.mode == KIND_DOWN) {
-                    mi = g / p.kc_total;
-                    c8 = g % p.kc_total;
-                } else {
-                    c8 = g;
-                }
+                const int c = __shfl_sync(0xffffffffu, code, sl);
+                const int mi = c & 15, c8 = (c >> 4) & 1023;
+                const int dx = ((c >> 14) & 3) - 1, dy = ((c >> 16) & 3) - 1, dz = ((c >> 18) & 3) - 1;
                 // one box brings ea consecutive chunk planes (runs never straddle a tap or source)
                 if (leader)
                     load_box(a_dst + gbytes * sl, &p.amaps[mi], full, p.mode == KIND_DOWN, c8, x0 + dx, y0 + dy,
@@ -557,6 +567,35 @@ namespace spnn {
 
 constexpr uint32_t kHaloRow = 18 * 16;   // bytes of one halo row: 16 voxels + 2 halo, 16 B each
 
+// The 3 nM MMAs of one halo weight-gradient K-step: accumulator (dx, row block
+// j) at columns (dx nM + j) n; dx is a 1-unit (16-byte) start offset of A,
+// row block j starts 16 rows (kHaloRow units) further.  Unrolled for the
+// common nM so that the MMAs issue back to back.
+template <int NM>
+__device__ __forceinline__ void issue_wgrad_halo_step(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t n,
+                                                      uint32_t idesc, uint32_t acc) {
+#pragma unroll
+    for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+            umma_bf16(tmem + (uint32_t)(dxi * NM + j) * n, ad + (uint32_t)(dxi + j * kHaloRow), bd, idesc, acc);
+}
+
+__device__ __forceinline__ void issue_wgrad_halo_step(int nM, uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t n,
+                                                      uint32_t idesc, uint32_t acc) {
+    switch (nM) {
+    case 1: issue_wgrad_halo_step<1>(tmem, ad, bd, n, idesc, acc); break;
+    case 2: issue_wgrad_halo_step<2>(tmem, ad, bd, n, idesc, acc); break;
+    case 3: issue_wgrad_halo_step<3>(tmem, ad, bd, n, idesc, acc); break;
+    case 4: issue_wgrad_halo_step<4>(tmem, ad, bd, n, idesc, acc); break;
+    case 5: issue_wgrad_halo_step<5>(tmem, ad, bd, n, idesc, acc); break;
+    default:
+        for (int dxi = 0; dxi < 3; ++dxi)
+            for (int j = 0; j < nM; ++j)
+                umma_bf16(tmem + (uint32_t)(dxi * nM + j) * n, ad + (uint32_t)(dxi + j * kHaloRow), bd, idesc, acc);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_constant__ WgradHaloParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
@@ -638,14 +677,9 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
             tc_fence_after();
             const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
             const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
-            // dx is a 16-byte (1 unit) start offset, row block j starts 16 rows of kHaloRow bytes further
             const uint64_t ad = smem_desc(a0, 128u, kHaloRow);
             if (leader) {
-#pragma unroll
-                for (int dxi = 0; dxi < 3; ++dxi)
-                    for (int j = 0; j < p.nM; ++j)
-                        umma_bf16(tmem + (uint32_t)((dxi * p.nM + j) * p.n), ad + (uint32_t)(dxi + j * kHaloRow), bd,
-                                  p.idesc, kk > 0 ? 1u : 0u);
+                issue_wgrad_halo_step(p.nM, tmem, ad, bd, (uint32_t)p.n, p.idesc, kk > 0 ? 1u : 0u);
                 umma_commit(bar0 + 8u * (S + s));
             }
             __syncwarp();
