@@ -391,7 +391,9 @@ def test_conv3_tilings_agree_with_oracle(S, subtiles, planes):
     check(np.concatenate([f64(dx0), f64(dx1)], axis=-1), g, ga, what="dgrad")
 
 
-@pytest.mark.parametrize("c0,c1,co,halo", [(32, 0, 32, 1), (32, 32, 32, 1), (16, 0, 32, 1), (32, 32, 32, 0)])
+# input channels 16 .. 80 give 2 .. 6 row blocks of 16 (tap, 8-channel) groups per x-shift
+@pytest.mark.parametrize("c0,c1,co,halo", [(32, 0, 32, 1), (32, 32, 32, 1), (16, 0, 32, 1), (32, 32, 32, 0),
+                                           (48, 0, 32, 1), (80, 0, 16, 1)])
 def test_conv3_wgrad_halo_kernel(S, c0, c1, co, halo):
     """conv3 weight and bias gradients with halo K-steps (all 27 taps from one
     box per 16-voxel row) and with the per-tap kernel, against the oracle."""
