@@ -550,10 +550,14 @@ int wgrad_halo(int B, int D, int H, int W, const void* x0, int c0, const void* x
     // A region: every row a tile can read, (16 nM + 1) rows of 288 bytes
     p.a_region = ((uint32_t)(16 * nM + 1) * 288u + 1023u) & ~1023u;
     p.b_stage_bytes = (uint32_t)cout * 32u;
-    p.stage_bytes = (p.a_region + p.b_stage_bytes + 1023u) & ~1023u;
     // resident CTAs per SM: TMEM columns, then the shared-memory ring
     const int ncols = (int)tmem_cols(3 * nM * cout);
     const int per_sm = 512 / ncols;
+    // with one CTA per SM, two K-steps per stage (one barrier handshake per 2 x 3 nM
+    // MMAs) measured 8-10 % faster; with two CTAs per SM the halved ring lost
+    p.ksub = per_sm > 1 ? 1 : 2;
+    p.sub_bytes = (p.a_region + p.b_stage_bytes + 1023u) & ~1023u;
+    p.stage_bytes = (uint32_t)p.ksub * p.sub_bytes;
     int S = (int)((uint32_t)(per_sm > 1 ? 100 : 200) * 1024u / p.stage_bytes);
     p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
     p.idesc = idesc_bf16(128, cout, 1, 1);

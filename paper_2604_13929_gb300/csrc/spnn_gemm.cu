@@ -612,9 +612,10 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
     const int kbeg = blockIdx.x * p.ksteps_per_cta;
     const int kend = min(kbeg + p.ksteps_per_cta, p.ksteps_total);
 
-    // the ones row of every stage (written once; TMA never writes it)
-    for (int s = 0; s < S; ++s) {
-        uint32_t* dst = reinterpret_cast<uint32_t*>(smem + (size_t)s * p.stage_bytes + (size_t)groups * kHaloRow);
+    // the ones row of every K-step region of every stage (written once; TMA never writes it)
+    for (int s = 0; s < S * p.ksub; ++s) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(smem + (size_t)(s / p.ksub) * p.stage_bytes +
+                                                    (size_t)(s % p.ksub) * p.sub_bytes + (size_t)groups * kHaloRow);
         for (int i = threadIdx.x; i < (int)(kHaloRow / 4); i += blockDim.x) dst[i] = 0x3F803F80u;
     }
     fence_async_shared();
@@ -642,32 +643,36 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
         Ring q;
         int x0, y0, z0, b0;
         tile_origin(p.g, kbeg, x0, y0, z0, b0);
-        for (int k = kbeg; k < kend; ++k, q.next(S), tile_next(p.g, x0, y0, z0, b0)) {
-            const int kk = k - kbeg;
+        // a stage holds ns <= ksub consecutive K-steps
+        for (int k = kbeg; k < kend; q.next(S)) {
+            const int ns = min(p.ksub, kend - k);
             const int s = q.s;
             const uint32_t r = q.r;
             const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
-            if (kk >= S && !__all_sync(0xffffffffu, mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs))) {
+            if (r > 0 && !__all_sync(0xffffffffu, mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs))) {
                 if (leader) atomicOr(p.err, ERR_TIMEOUT);
                 break;
             }
-            const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-            if (leader) {
-                mbar_expect_tx(full, tx);
-                tma_load_5d(a_dst, &p.amaps[0], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, 0);
-                if (p.kc1)
-                    tma_load_5d(a_dst + (uint32_t)p.kc0 * 9u * kHaloRow, &p.amaps[1], full, 8 * (x0 - 1), y0 - 1,
-                                z0 - 1, b0, 0);
-                tma_load_5d(a_dst + p.a_region, &p.bmap, full, 8 * x0, y0, z0, b0, 0);
+            if (leader) mbar_expect_tx(full, (uint32_t)ns * tx);
+            for (int j = 0; j < ns; ++j, tile_next(p.g, x0, y0, z0, b0)) {
+                const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes + (uint32_t)j * p.sub_bytes;
+                if (leader) {
+                    tma_load_5d(a_dst, &p.amaps[0], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, 0);
+                    if (p.kc1)
+                        tma_load_5d(a_dst + (uint32_t)p.kc0 * 9u * kHaloRow, &p.amaps[1], full, 8 * (x0 - 1),
+                                    y0 - 1, z0 - 1, b0, 0);
+                    tma_load_5d(a_dst + p.a_region, &p.bmap, full, 8 * x0, y0, z0, b0, 0);
+                }
             }
+            k += ns;
             __syncwarp();
         }
     } else if (warp == 1) {
         // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
         const bool leader = elect_one();
         Ring q;
-        for (int k = kbeg; k < kend; ++k, q.next(S)) {
-            const int kk = k - kbeg;
+        for (int k = kbeg; k < kend; q.next(S)) {
+            const int ns = min(p.ksub, kend - k);
             const int s = q.s;
             const uint32_t r = q.r;
             if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
@@ -675,13 +680,15 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
                 break;
             }
             tc_fence_after();
-            const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
-            const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
-            const uint64_t ad = smem_desc(a0, 128u, kHaloRow);
-            if (leader) {
-                issue_wgrad_halo_step(p.nM, tmem, ad, bd, (uint32_t)p.n, p.idesc, kk > 0 ? 1u : 0u);
-                umma_commit(bar0 + 8u * (S + s));
+            for (int j = 0; j < ns; ++j) {
+                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes + (uint32_t)j * p.sub_bytes;
+                const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
+                const uint64_t ad = smem_desc(a0, 128u, kHaloRow);
+                if (leader)
+                    issue_wgrad_halo_step(p.nM, tmem, ad, bd, (uint32_t)p.n, p.idesc, (k > kbeg || j > 0) ? 1u : 0u);
             }
+            if (leader) umma_commit(bar0 + 8u * (S + s));
+            k += ns;
             __syncwarp();
         }
         if (leader) umma_commit(done);

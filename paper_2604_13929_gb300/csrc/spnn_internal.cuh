@@ -132,7 +132,8 @@ struct WgradHaloParams {
     int kc0, kc1, n, nM;
     TileGrid g;                     // 16-voxel x-runs of the grid
     int ksteps_total, ksteps_per_cta, stages;
-    uint32_t a_region, b_stage_bytes, stage_bytes;
+    int ksub;                       // K-steps per stage (each its own a_region + B block, sub_bytes apart)
+    uint32_t a_region, b_stage_bytes, sub_bytes, stage_bytes;
     uint32_t idesc;
     float* dw;                      // [27][8 * (kc0 + kc1)][n]
     float* db;                      // [n] or null
