@@ -1,14 +1,21 @@
-// spnn_gemm.cu -- the two tensor-core GEMM kernels of the surrogate.
+// spnn_gemm.cu -- the tensor-core GEMM kernels of the surrogate: rows_kernel
+// (forward and input-gradient layers), wgrad_kernel and wgrad_halo_kernel
+// (weight gradients).
 //
-// Both are warp-specialised, one CTA per output tile, 192 threads:
+// All are warp-specialised, 192 threads:
 //   warp 0      TMA producer: fills a ring of shared-memory stages,
-//   warp 1      allocates TMEM and issues tcgen05.mma from one thread,
+//   warp 1      allocates TMEM and issues tcgen05.mma,
 //   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulators, fused
-//               bias / residual / ReLU / ReLU-derivative mask, BF16 stores.
-// Stages hand over with mbarriers: "full" completes when TMA bytes land,
-// "empty" when the MMAs that read the stage retire (tcgen05.commit).  Every
-// wait is bounded by kWaitLimitNs; a timeout sets an error flag, and the CTA
-// still releases its TMEM and exits.
+//               bias / residual / ReLU / ReLU-derivative mask, BF16 stores
+//               (FP32 atomics for weight gradients).
+// The MMA warp (and the weight-gradient producers) walk their K loop with all
+// 32 lanes so that descriptor and coordinate arithmetic stays warp-uniform; one
+// elected lane issues.  K loops carry their stage index and tile origin as
+// running values: integer division per step costs a lone thread hundreds of
+// cycles.  Stages hand over with mbarriers: "full" completes when TMA bytes
+// land, "empty" when the MMAs that read the stage retire (tcgen05.commit).
+// Every wait is bounded by kWaitLimitNs; a timeout sets an error flag, and the
+// CTA still releases its TMEM and exits.
 #include "spnn_internal.cuh"
 #include "spnn_umma.cuh"
 
