@@ -3,7 +3,7 @@
 The surrogate (``spnn.UNet``) learns ln(Phi/S0) per voxel from Monte Carlo
 fields of the transport engine (``spmc``) on Cahn-Hilliard masks with random
 porosity and solid optics, so that mask designs (Sec. 5 of arXiv 2604.13929)
-can be screened without a photon run.  It is judged on held-out masks by the
+can be screened without a photon run.  It is scored on held-out masks by the
 fluence-weighted relative RMS deviation (Eq. RMSw) of its per-phase depth
 profiles from the Monte Carlo ones, and by fields per second.
 
