@@ -124,3 +124,34 @@ def test_surrogate_options_are_validated_without_a_device(nnlib):
     for key in ("conv_subtiles", "conv_planes", "stage_kb", "wgrad_halo", "conv_full_halo"):
         assert nnlib.spnn_set_option(spnn.OPT[key], 0) == spnn.SPNN_OK
     assert nnlib.spnn_set_option(spnn.OPT["wgrad_halo"], 1) == spnn.SPNN_OK
+
+
+def _header_constants(path, prefix):
+    """NAME -> value of every `prefix`* constant a header defines (#define or enum)."""
+    text = re.sub(r"/\*.*?\*/", " ", open(path).read(), flags=re.S)   # drop comments
+    out = {m.group(1): int(m.group(2)) for m in re.finditer(rf"#define\s+({prefix}\w*)\s+\(?(-?\d+)\)?", text)}
+    out.update({m.group(1): int(m.group(2)) for m in re.finditer(rf"\b({prefix}\w*)\s*=\s*(-?\d+)", text)})
+    return out
+
+
+def test_binding_option_keys_match_the_headers():
+    import os
+    from paper_2604_13929_gb300 import spnn
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sp = _header_constants(os.path.join(root, "include", "spmc.h"), "SP_OPT_")
+    nn = _header_constants(os.path.join(root, "include", "spnn.h"), "SPNN_OPT_")
+    assert {"SP_OPT_" + k.upper(): v for k, v in spmc.OPT.items()} == sp
+    assert {"SPNN_OPT_" + k.upper(): v for k, v in spnn.OPT.items()} == nn
+
+
+def test_binding_status_codes_match_the_headers():
+    import os
+    from paper_2604_13929_gb300 import spnn
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sp = _header_constants(os.path.join(root, "include", "spmc.h"), "SP_E")
+    sp.update(_header_constants(os.path.join(root, "include", "spmc.h"), "SP_OK"))
+    nn = _header_constants(os.path.join(root, "include", "spnn.h"), "SPNN_E")
+    nn.update(_header_constants(os.path.join(root, "include", "spnn.h"), "SPNN_OK"))
+    assert sp == {n: getattr(spmc, n) for n in ("SP_OK", "SP_EINVAL", "SP_ENOMEM", "SP_ECUDA", "SP_ESTEPLIMIT",
+                                                 "SP_EOVERFLOW")}
+    assert nn == {n: getattr(spnn, n) for n in ("SPNN_OK", "SPNN_EINVAL", "SPNN_ENOMEM", "SPNN_ECUDA")}
