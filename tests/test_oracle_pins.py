@@ -166,9 +166,33 @@ def test_all_pore_mask_gives_unit_transmission_and_fluence():
     assert all(orc.exact_sum(res["field"][z]) == 4000 * 2 ** 32 for z in range(nz))
     assert np.all(n["depth"][1][(np.arange(nz) * 64) // nz] == 1.0)
     assert n["pore_path_mean"] == nz
+    # every escaping photon has P = nz: sum(w P^2)/sum(w) = nz^2 exactly
+    assert n["pore_path_m2"] == nz * nz
+    assert res["sum_wP2"] == 4000 * nz * nz * 2 ** 16
     h = res["hist"]
     assert h[64] == 4000 * 2 ** 32 and h.sum() == h[64]
     assert res["counts"]["interactions"] == 0
+
+
+def test_pore_path_moments_of_straight_rays():
+    """mu_s = 0 through laterally uniform layers: every photon runs straight
+    down, crosses n_p pore layers (P = n_p) and leaves with w = exp(-mu_a n_s)
+    after n_s solid layers.  The exit-weighted first and second pore-path
+    moments are then n_p and n_p^2, up to the Q32.32 / Q48.16 quantisation of
+    the single per-photon contribution (checks the weight factor, the square
+    and the 2^16 scale of the second moment)."""
+    pattern = [1, 0, 1, 1, 0, 0, 1, 1, 1, 0, 1]
+    n_p, n_s, mua, N = pattern.count(1), pattern.count(0), 0.3, 2000
+    res = orc.run(inputs.layered(pattern, 3, 4), 0.0, mua, 0.7, N, 8)
+    n = orc.normalise(res)
+    w = math.exp(-mua * n_s)
+    assert abs(n["T"] - w) <= 2.0 ** -33          # one Q32.32 rounding per photon
+    assert abs(n["pore_path_mean"] - n_p) < 2.0 ** -31 / w
+    assert abs(n["pore_path_m2"] - n_p ** 2) < 2.0 ** -15 / w
+    # the escape weight and the histogram put all weight at P = n_p
+    h = res["hist"]
+    b = int(n_p / (4.0 * len(pattern)) * 256)
+    assert h[b] == h.sum() and abs(h[b] / 2.0 ** 32 / N - w) < 1e-9
 
 
 def test_depth_bins_with_ragged_nz():
