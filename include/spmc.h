@@ -274,8 +274,8 @@ void sp_mc_batch_destroy(sp_mc_batch_t *b);
  * One complete simulation that allocates nothing.  The paper has no
  * counterpart to this entry point; it exists for callers that cannot call
  * cudaMalloc or any allocating routine: for instance code embedded in an
- * application whose own allocator owns all device memory, code that runs
- * while a stream is being captured, or latency-critical loops.
+ * application whose own allocator owns all device memory, or
+ * latency-critical loops that cannot afford an allocator call.
  *
  *   d_mask     DEVICE pointer, nz*ny*nx bytes, x fastest, nonzero = pore;
  *              read only, owned by the caller.
@@ -284,19 +284,21 @@ void sp_mc_batch_destroy(sp_mc_batch_t *b);
  *   voxel_h, mu_s, mu_a, g   as for sp_mc_create.
  *   n_photons, seed          photon ids 0 .. n_photons-1, Philox key = seed.
  *   out        HOST pointer to the caller's result struct (filled).
- *   stream     cudaStream_t or NULL; the call synchronises it.
+ *   stream     cudaStream_t or NULL.  The call synchronises it twice: once
+ *              to read the per-bin voxel counts back (they give the
+ *              porosity, which sets the path cap) and once for the result.
  * Runs with the default options of a fresh handle in the depth-profile tally
  * mode (SP_OPT_TALLY_FIELD = 0): R/T/A, estimators, depth profiles and the
  * pore-path statistics are produced, the voxel field is not.  Results equal
  * those of sp_mc_create/sp_mc_run/sp_mc_tallies with that option.
  *
  * Working memory is one fixed array of about 2.03 MiB inside the library,
- * held by every GPU that loads it until the process exits.  The first call
- * on a device looks up that array's device address (once per device, with
- * the device current); make that first call before any stream capture.
- * Every call reuses the array and clears what must start at zero, so calls
- * whose GPU work overlaps (other streams, other host threads) race and must
- * be serialised by the caller.  Returns SP_OK or a negative SP_E* code.
+ * held by every GPU that loads it until the process exits.  Every call looks
+ * up that array's device address on the current device (which allocates
+ * nothing), so the address stays right across a device reset.  Every call
+ * reuses the array and clears what must start at zero, so calls whose GPU
+ * work overlaps (other streams, other host threads) race and must be
+ * serialised by the caller.  Returns SP_OK or a negative SP_E* code.
  */
 int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int nz, double voxel_h,
                            double mu_s, double mu_a, double g, uint64_t n_photons,

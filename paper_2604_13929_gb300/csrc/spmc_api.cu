@@ -14,7 +14,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -827,12 +826,11 @@ int sp_mc_restore(sp_mc_t *h, const void *buf, size_t size, void *stream) {
 // Allocation-free entry point.
 //
 // For callers that may not allocate device memory themselves, e.g. code
-// embedded in a host application whose allocator owns all device memory,
-// code running while a stream is being captured, or latency-critical loops
-// that cannot afford an allocator call.  Its working memory is the fixed
-// array below, which every GPU that loads this library keeps until the
-// process exits.  The paper has no counterpart to this; it is an interface
-// convenience around the same transport kernel.
+// embedded in a host application whose own allocator owns all device memory,
+// or latency-critical loops that cannot afford an allocator call.  Its
+// working memory is the fixed array below, which every GPU that loads this
+// library keeps until the process exits.  The paper has no counterpart to
+// this; it is an interface convenience around the same transport kernel.
 // ------------------------------------------------------------------------
 
 namespace {
@@ -846,15 +844,11 @@ constexpr size_t kOffCount = align_up(kOffTal + sizeof(DevTallies));
 constexpr size_t kOffResult = align_up(kOffCount + 2 * kNBin * sizeof(u64));
 constexpr size_t kScratchBytes = align_up(kOffResult + sizeof(sp_mc_result_t));
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned char *g_noalloc_ptr[kMaxDevices] = {};
-
 }  // namespace
 
 // The scratch array (about 2.03 MiB).  Host code must not pass its name to a
 // kernel: on the host it is only a stand-in symbol, so its device address is
-// looked up once per device with cudaGetSymbolAddress.
+// looked up with cudaGetSymbolAddress on the current device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Pore voxels per depth bin (phase 1) and solid voxels (phase 0).
@@ -889,25 +883,20 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     const u64 nbx = (u64)(nx + 3) / 4, nby = (u64)(ny + 3) / 4, nbz = (u64)(nz + 3) / 4;
     if (nbx * nby * nbz > kNoAllocMaxBricks) return fail(SP_EINVAL, "size too large");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return fail(SP_ECUDA, "no CUDA device");
     }
-    unsigned char *base = nullptr;
-    {
-        // First call on this device: look up the array's device address
-        // (with this device current).  Later calls reuse it.
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
-            void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return fail(SP_ECUDA, "symbol lookup");
-            }
-            g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
-        }
-        base = g_noalloc_ptr[dev];
+    // Set-up, repeated on every call with the caller's device current: the
+    // array's device address.  The lookup allocates nothing, and doing it
+    // each time keeps the address right after a device reset or a new
+    // context, where the module (and the array) may have moved.
+    void *sym = nullptr;
+    if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) {
+        cudaGetLastError();
+        return fail(SP_ECUDA, "symbol lookup");
     }
+    unsigned char *base = static_cast<unsigned char *>(sym);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     u64 *bricks = reinterpret_cast<u64 *>(base + kOffBricks);
     DevTallies *tal = reinterpret_cast<DevTallies *>(base + kOffTal);
@@ -935,7 +924,8 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     for (int b = 0; b < kNBin; ++b) n_pore += cnt[kNBin + b];
     const double porosity = (double)n_pore / ((double)nx * (double)ny * (double)nz);
 
-    // Default options of a fresh handle, profile-only tally (no voxel field).
+    // Default options of a fresh handle, profile-only tally (no voxel field);
+    // the launch constants come from the same helpers as sp_mc_run's.
     sp_mc tmp;
     tmp.nx = nx; tmp.ny = ny; tmp.nz = nz;
     tmp.mus = mu_s * voxel_h; tmp.mua = mu_a * voxel_h; tmp.g = g;
@@ -961,26 +951,8 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     p.rr_mult = tmp.rr_mult;
     p.iter_limit = iter_limit(&tmp);
     p.compact_k = tmp.compact_k;
-    p.hg_iso = std::fabs(g) < 1e-6;
-    p.small_x = tmp.mua * 1.7320508075688772 <= 0.1;
-    p.f32.mus = (float)tmp.mus;
-    p.f32.mua = (float)tmp.mua;
-    p.f32.inv_mus = tmp.mus > 0 ? (float)(1.0 / tmp.mus) : 0.0f;
-    p.f32.inv_mua = tmp.mua > 0 ? (float)(1.0 / tmp.mua) : 0.0f;
-    {
-        const float gf = (float)g;
-        p.f32.one_m_g2 = 1.0f - gf * gf;
-        p.f32.one_p_g2 = 1.0f + gf * gf;
-        p.f32.one_m_g = 1.0f - gf;
-        p.f32.two_g = 2.0f * gf;
-        p.f32.inv_2g = p.hg_iso ? 0.0f : (float)(1.0 / (2.0 * g));
-    }
-    p.f32.s_max = (float)p.s_max;
-    p.f32.rr_weight = (float)tmp.rr_weight;
-    p.f32.rr_mult = (float)tmp.rr_mult;
-    p.f32.rr_p = (float)(1.0 / tmp.rr_mult);
-    p.f32.rr_gain = (float)(tmp.rr_mult - 1.0);
-    p.f32.hist_scale = (float)(256.0 / (4.0 * (double)nz));
+    p.mirror = 0;
+    fill_f32(&tmp, p.s_max, p.f32, p.hg_iso, p.small_x);
 
     if (n_photons > 0 && launch_transport_f32(p, false, per_sm * sms, tmp.threads, 0, s) != cudaSuccess)
         return fail(SP_ECUDA, "CUDA error");

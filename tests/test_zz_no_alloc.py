@@ -66,6 +66,41 @@ def test_no_alloc_entry_point_matches_handle_api_twice(setup):
         assert got["photons"] == n and got["status"] == 0
 
 
+def test_no_alloc_ragged_sides_after_a_different_volume(setup):
+    """Sides that are not multiples of 4 (partial bricks in the packing and
+    the voxel counts), called right after a call on a different volume, then
+    again: each result equals the handle API's."""
+    torch, spmc, mask = setup
+    ragged = inputs.spinodal_mask((37, 33, 41), 0.80, 300, seed=4, device="cuda")
+    n, seed = 40000, 77
+    ref = _reference(spmc, ragged, n, seed)
+    d_big = torch.from_numpy(np.ascontiguousarray(mask)).cuda()
+    d_rag = torch.from_numpy(np.ascontiguousarray(ragged)).cuda()
+    nz, ny, nx = mask.shape
+    spmc.sp_mc_simulate_noalloc(d_big, nx, ny, nz, 1.0, MUS, MUA, G, 5000, 1)
+    for _ in range(2):
+        got = spmc.sp_mc_simulate_noalloc(d_rag, 41, 33, 37, 1.0, MUS, MUA, G, n, seed)
+        _same(got, ref)
+
+
+def test_no_alloc_limit_is_exactly_2_pow_18_bricks(setup):
+    """256^3 (exactly 2^18 bricks) is accepted and matches the handle API;
+    one more z-layer (65 brick layers) is refused on the host with a buffer
+    of the full size behind the pointer."""
+    torch, spmc, _ = setup
+    mask = inputs.random_mask((256, 256, 256), 0.9, 6)
+    n, seed = 20000, 5
+    ref = _reference(spmc, mask, n, seed)
+    d_mask = torch.from_numpy(mask).cuda()
+    got = spmc.sp_mc_simulate_noalloc(d_mask, 256, 256, 256, 1.0, MUS, MUA, G, n, seed)
+    _same(got, ref)
+    del d_mask
+    d_over = torch.zeros((257, 256, 256), dtype=torch.uint8, device="cuda")
+    with pytest.raises(spmc.SpmcError) as e:
+        spmc.sp_mc_simulate_noalloc(d_over, 256, 256, 257, 1.0, MUS, MUA, G, n, seed)
+    assert e.value.code == spmc.SP_EINVAL and "too large" in str(e.value)
+
+
 def test_no_alloc_entry_point_rejects_oversized_volumes(setup):
     """Volumes above the documented 2^18-brick limit are refused on the host,
     before any device work (the mask pointer is never read)."""
