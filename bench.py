@@ -37,21 +37,48 @@ METRIC = "photons/s & voxel-steps/s at 256³ φ=0.9"
 WORKLOAD = ("256^3 Cahn-Hilliard spinodal mask (dt 0.1, 4000 steps, seed 0), porosity 0.90; "
             "solid mu_s h 0.5, mu_a h 0.005, HG g 0.7; pores void; periodic x/y; "
             "1e8 photons per step; FP32 transport; Q32.32 voxel fluence field")
-# Algorithmic lane-operations per unit of work (derivation in the design notes):
-# a voxel step, an interaction event and a photon launch.
-OPS_STEP, OPS_INTERACT, OPS_LAUNCH = 30, 120, 90
+# Algorithmic lane-operations per unit of work: the method's own operations
+# (Sec. 2.5 transport step, interaction and photon life cycle), not the
+# compiled code's.  The same table, term by term, is in the design doc section 6:
+#   any voxel step   26 = next face 4 (two compares, two selects), segment 1,
+#                    path cap 2, deposit 6 (multiply, quantise 2, address 2,
+#                    RED 1), path 1, crossing 9 (face parameter 1, index 2,
+#                    wrap 2, brick and bit address 4), phase bit 2, pore path 1
+#   solid step      +11 = optical depth 3 (multiply, compare, subtract) and
+#                    Beer-Lambert 8 (mu_a l, 1 - e^-x as a quartic 4, dA,
+#                    A += dA, w -= dA)  -> 37 in total
+#   interaction    130 = Philox4x32-10 40 (10 rounds x 2 wide multiplies and
+#                    2 three-way XORs), 4 uniforms 12, roulette 2, HG 7,
+#                    azimuth 3, sin theta 3, rotation 25, renormalise 8,
+#                    new optical depth 2, ray set-up 15, position in voxel 12
+#   photon         100 = launch (Philox 40, uniforms 12, position 6, optical
+#                    depth 2, state 15, brick 6, claim 3) and exit tallies 16
+OPS_STEP, OPS_SOLID_EXTRA, OPS_INTERACT, OPS_PHOTON = 26, 11, 130, 100
+# special-function (SFU / XU pipe) operations per unit: interaction 10 (HG
+# reciprocal, sine and cosine, square root, two reciprocal square roots,
+# logarithm, three reciprocals), photon 1 (logarithm); none per step (the
+# Beer-Lambert factor is a polynomial)
+SFU_INTERACT, SFU_PHOTON = 10, 1
 ISSUE_PER_SM_CLK = 4          # warp instructions per SM per clock (4 schedulers)
+SFU_PER_SM_CLK = 16           # XU lane-operations per SM per clock
 # DRAM bytes (read + write) per photon of the transport kernel from one ncu capture
 # (2e7 photons of this workload), valid only for the kernel source it was taken on.
 TRAFFIC_CAPTURE = {"kernel_sha256_prefix": "e811141632e4586f", "dram_bytes_per_photon": 16287.6,
                    "source": "profiles/transport_kernel_256cubed_phi090.md"}
+# Hardware fractions of peak of the transport kernel from one ncu capture of a
+# 2e6-photon launch of this workload (issue slots, XU pipe, L2 atomic unit);
+# reported only while the kernel source matches the capture.
+NCU_FRACTIONS = None
 
 
 def _kernel_sha_prefix():
+    """Hash of the transport kernel sources (generic template and FP32 kernel)."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2604_13929_gb300", "csrc", "spmc_transport.cuh")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("spmc_transport.cuh", "spmc_transport_f32.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_13929_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _env_int(name, default):
@@ -107,9 +134,49 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_mask(device):
+def make_masks(device):
+    """The 256^3 Cahn-Hilliard field (4000 steps, seed 0) thresholded at the
+    headline porosity 0.90 and at 0.70 (the same field, as the paper's pair)."""
     from paper_2604_13929_gb300 import inputs
-    return inputs.spinodal_mask(N_VOX, POROSITY, CH_STEPS, seed=0, device=device)
+    c = inputs.cahn_hilliard((N_VOX,) * 3, CH_STEPS, seed=0, device=device)
+    m90 = inputs.rank_threshold(c, POROSITY)
+    m70 = inputs.rank_threshold(c, 0.70)
+    del c
+    return m90, m70
+
+
+def make_mask(device):
+    return make_masks(device)[0]
+
+
+def other_workloads(spmc, torch, stream, m70, photons):
+    """256^3 phi = 0.70 (same Cahn-Hilliard field) and homogeneous 256^3 slabs
+    at the optics matched to phi = 0.90 and 0.70 (mu h (1 - phi), Eq.
+    EMA_scaling): photons/s, voxel-steps/s and the estimators, one warm-up and
+    one timed launch each, full Q32.32 field as in the headline."""
+    from paper_2604_13929_gb300 import inputs
+    slab = inputs.all_solid(N_VOX, N_VOX, N_VOX)
+    cases = [("spinodal_phi0.70", m70, MUS, MUA),
+             ("slab_matched_phi0.90", slab, MUS * (1 - POROSITY), MUA * (1 - POROSITY)),
+             ("slab_matched_phi0.70", slab, MUS * 0.30, MUA * 0.30)]
+    out = {}
+    for name, mask, mus, mua in cases:
+        sim = spmc.Simulation(mask, mus, mua, G)
+        sim.run(photons // 10, SEED + 1, stream)
+        sim.reset(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(photons, SEED, stream)
+        e1.record(stream)
+        t = sim.tallies(stream)
+        sim.close()
+        sec = e0.elapsed_time(e1) / 1e3
+        out[name] = {"mu_s_h": mus, "mu_a_h": mua, "photons": photons,
+                     "photons_per_s": photons / sec, "voxel_steps_per_s": t["steps"] / sec,
+                     "steps_per_photon": t["steps"] / photons,
+                     **{k: t[k] for k in ("R", "T", "A", "R_se", "T_se", "A_se", "closure", "phi_3d",
+                                          "phi_1d", "r", "ratio", "pore_path_mean", "porosity")}}
+    return out
 
 
 def cpu_baseline(mask, target_s=15.0):
@@ -177,22 +244,35 @@ def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
     # the autotuner times each candidate on a tenth of a step: large enough that
     # per-launch overheads weigh as they do in the timed steps
     tuned = b.autotune([n_each // 10] * len(problems), SEED + 7, stream)
-    for _ in range(args.warmup):
-        b.run([n_each] * len(problems), SEED + rank, stream)
-    torch.cuda.synchronize()
-    b.reset(stream)
-    barrier()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local_rank) as clk:
-        start.record(stream)
-        for _ in range(args.steps):
+    tuned_mode = int(b.get_option("batch_mode"))
+
+    def timed(mode):
+        b.set_option("batch_mode", mode)
+        for _ in range(args.warmup):
             b.run([n_each] * len(problems), SEED + rank, stream)
-        stop.record(stream)
         torch.cuda.synchronize()
+        b.reset(stream)
         barrier()
-    ms = start.elapsed_time(stop)
-    steps = sum(b.tallies(i, stream)["steps"] for i in range(len(problems)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local_rank) as clk_:
+            e0.record(stream)
+            for _ in range(args.steps):
+                b.run([n_each] * len(problems), SEED + rank, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        st = sum(b.tallies(i, stream)["steps"] for i in range(len(problems)))
+        b.reset(stream)
+        return e0.elapsed_time(e1), st, clk_
+
+    # both strategies at the autotuned launch shape; the headline is the
+    # tuned one, the one-launch number is reported beside it
+    other = 1 - tuned_mode
+    ms_o, _, _ = timed(other)
+    ms, steps, clk = timed(tuned_mode)
+    b.set_option("batch_mode", tuned_mode)
     photons = n_each * len(problems) * args.steps * world
+    by_mode = {tuned_mode: photons / world / (ms / 1e3), other: photons / world / (ms_o / 1e3)}
     # the same problems one launch at a time (sp_mc_run per mask), for comparison
     sims = [spmc.Simulation(m, mus, mua, g) for (m, mus, mua, g) in problems]
     for sim in sims:
@@ -215,9 +295,11 @@ def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
                                    "64^3..256^3, porosity U[0.5,0.95], mu_s h logU[0.1,2], "
                                    "mu_a h U[0.001,0.05], g U[0,0.9]; 1e7 photons each per step; "
                                    "one persistent launch per step, CUDA graph replay",
-                       "launch": {k: b.get_option(k) for k in ("threads", "blocks", "compact", "batch_mode")},
+                       "launch": {k: b.get_option(k) for k in ("threads", "blocks", "compact", "batch_mode",
+                                                               "kernel", "steps_per_pass")},
                        "autotune_photons_per_s": tuned, "mask_generation_s": gen_s},
             "voxel_steps_per_s": steps * world / (ms / 1e3),
+            "one_launch_photons_per_s": by_mode[0], "per_problem_launches_photons_per_s": by_mode[1],
             "sequential_photons_per_s": seq_rate,
             "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
     b.close()
@@ -458,6 +540,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the phi=0.70 and matched-slab throughput keys")
     ap.add_argument("--workload", default="c2", choices=["c2", "batch", "paper", "precision", "surrogate"],
                     help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
                          "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
@@ -515,7 +599,7 @@ def main():
             else:
                 surrogate_bench(torch, args)
         return
-    mask = make_mask("cuda")
+    mask, mask70 = make_masks("cuda")
     stream = torch.cuda.current_stream()
     if args.profile_launch:
         prof = spmc.Simulation(mask, MUS, MUA, G)
@@ -584,25 +668,41 @@ def main():
 
     # roofline of the transport kernel: algorithmic lane-operations / issue peak
     launch_ms = statistics.mean(kernel_ms)
-    ops = (OPS_STEP * last["steps"] + OPS_INTERACT * last["interactions"]
-           + OPS_LAUNCH * last["launched"]) / 32.0         # warp-instruction equivalents
+    ops = (OPS_STEP * last["steps"] + OPS_SOLID_EXTRA * last["solid_steps"]
+           + OPS_INTERACT * last["interactions"] + OPS_PHOTON * last["launched"]) / 32.0
+    sfu = SFU_INTERACT * last["interactions"] + SFU_PHOTON * last["launched"]
     props = torch.cuda.get_device_properties(local_rank)
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak = props.multi_processor_count * ISSUE_PER_SM_CLK * max_mhz * 1e6
+    sfu_peak = props.multi_processor_count * SFU_PER_SM_CLK * max_mhz * 1e6
     achieved = ops / (launch_ms / 1e3)
+    sha = _kernel_sha_prefix()
     traffic = None
-    if _kernel_sha_prefix() == TRAFFIC_CAPTURE["kernel_sha256_prefix"]:
+    if sha == TRAFFIC_CAPTURE["kernel_sha256_prefix"]:
         traffic = TRAFFIC_CAPTURE["dram_bytes_per_photon"] * args.photons
+    variant = int(sim.get_option("kernel"))
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "DRAM read+write bytes per launch, ncu capture of 2e7 photons "
-                                "scaled by the photon count (null if the kernel changed since)",
-                "kernel": "spmc::transport_kernel<float,true,false,false>",
+                "traffic_note": "DRAM read+write bytes per launch, ncu capture scaled by the "
+                                "photon count (null if the kernel source changed since)",
+                "kernel": ("spmc::transport_f32_kernel<true,false>" if variant == 1
+                           else "spmc::transport_kernel<float,true,false,false>"),
+                "kernel_sha256_prefix": sha,
+                "ops_per_unit": {"voxel_step": OPS_STEP, "solid_step_extra": OPS_SOLID_EXTRA,
+                                 "interaction": OPS_INTERACT, "photon": OPS_PHOTON},
+                "units_per_launch": {"voxel_steps": last["steps"], "solid_steps": last["solid_steps"],
+                                     "interactions": last["interactions"], "photons": last["launched"]},
                 "peak_source": f"{props.multi_processor_count} SMs x {ISSUE_PER_SM_CLK} "
                                f"warp-inst/clk x {max_mhz:.0f} MHz (max SM clock)",
                 "launch_ms": launch_ms,
                 "frac_at_measured_clock": (achieved / (peak * clocks["sm_mhz"] / max_mhz)
-                                           if clocks["sm_mhz"] else None)}
+                                           if clocks["sm_mhz"] else None),
+                "sfu": {"achieved_gops": sfu / (launch_ms / 1e3) / 1e9, "peak_gops": sfu_peak / 1e9,
+                        "frac": sfu / (launch_ms / 1e3) / sfu_peak,
+                        "peak_source": f"{props.multi_processor_count} SMs x {SFU_PER_SM_CLK} "
+                                       f"XU lane-ops/clk x {max_mhz:.0f} MHz"},
+                "ncu_fractions": (NCU_FRACTIONS if NCU_FRACTIONS
+                                  and NCU_FRACTIONS.get("kernel_sha256_prefix") == sha else None)}
 
     # measured ceiling of the step pattern: straight rays through an all-pore
     # 256^3 volume, with and without one Q32.32 RED per step into a 256^3 field
@@ -656,6 +756,8 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_other_workloads:
+        line["other_workloads"] = other_workloads(spmc, torch, stream, mask70, args.photons)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mask.copy(), target_s=args.cpu_seconds)
         line["cpu_baseline"].pop("photons", None)

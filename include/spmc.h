@@ -81,11 +81,24 @@ enum sp_option {
     SP_OPT_LATERAL_BC  = 14, /* 0 (default): periodic x and y; 1: specular
                                 mirrors on the lateral faces (the paper's
                                 bc = "mmamma", Sec. 2.5)                  */
-    SP_OPT_BATCH_MODE  = 15  /* batched launches only: 0 (default) one
+    SP_OPT_BATCH_MODE  = 15, /* batched launches only: 0 (default) one
                                 persistent launch over all problems; 1 one
                                 single-problem launch per problem (shared-
                                 memory mask slab and tallies), still one
                                 graph replay per run                      */
+    SP_OPT_KERNEL      = 16, /* FP32 transport kernel: 1 (default) the
+                                streamlined kernel (several voxel steps per
+                                warp vote, branch-free phases, all events in
+                                the compacted event phase); 0 the generic
+                                template kernel (same photons, same method) */
+    SP_OPT_STEPS_PER_PASS = 17, /* streamlined kernel: voxel steps a lane
+                                takes per pass of its warp, [1, 64] (8);
+                                results do not depend on it                */
+    SP_OPT_L2_PERSIST  = 18  /* 1: persisting-L2 access-policy window over
+                                the voxel field for FP32 field launches
+                                (raises this process's persisting set-aside
+                                to the device maximum); 0 (default): none;
+                                results do not depend on it                */
 };
 
 typedef struct sp_mc sp_mc_t;   /* opaque, owned by the library */
@@ -115,6 +128,7 @@ typedef struct {
     /* integer event counts */
     uint64_t launched, interactions, scatters, rr_survive, rr_kill;
     uint64_t exit_R, exit_T, gated_n, steps;
+    uint64_t solid_steps;           /* voxel steps inside solid voxels      */
     /* raw Q32.32 tallies (exact), per batch slot pid % 16 */
     uint64_t raw_R[SP_NBATCH], raw_T[SP_NBATCH], raw_A[SP_NBATCH];
     uint64_t raw_gated[SP_NBATCH], raw_lost[SP_NBATCH], raw_gain[SP_NBATCH];
@@ -230,10 +244,14 @@ size_t sp_mc_result_size(void);
  * Many masks of uneven size and optics transported in ONE persistent launch
  * (the batched pattern of the design sweeps; the paper runs its cases one at
  * a time).  Each problem has its own bit-packed mask, Q32.32 voxel field and
- * integer tallies, exactly as an sp_mc_create handle; photons of all problems
- * are claimed from one counter, so lanes carry photons of different problems.
- * With the same seed and photon counts every problem's tallies equal those of
- * a separate sp_mc_run on its own handle, bit for bit.
+ * integer tallies, exactly as an sp_mc_create handle.  With the streamlined
+ * kernel (SP_OPT_KERNEL = 1, default) every warp claims chunks of 2048
+ * photons of one problem from a shared counter and keeps that problem's
+ * tallies in shared memory until it moves on; with the generic kernel (0)
+ * photons of all problems are claimed one by one, so lanes of a warp carry
+ * different problems.  With the same seed and photon counts every problem's
+ * tallies equal those of a separate sp_mc_run on its own handle (same kernel
+ * variant), bit for bit.
  */
 typedef struct sp_mc_batch sp_mc_batch_t;
 
@@ -244,7 +262,9 @@ sp_mc_batch_t *sp_mc_batch_create(int n, const uint8_t *const *masks, const int 
                                   const double *optics);
 /* SP_OPT_THREADS (threads per CTA, default 128), SP_OPT_BLOCKS (CTAs per SM,
  * 0 = as many as fit), SP_OPT_COMPACT, SP_OPT_GRAPH and SP_OPT_BATCH_MODE
- * apply to the launch (in mode 1 every problem uses its own launch options); the
+ * apply to the launch (in mode 1 every problem uses its own launch options);
+ * SP_OPT_KERNEL and SP_OPT_STEPS_PER_PASS apply to the one launch and to
+ * every problem's own launches; the
  * path-cap, roulette and iteration-limit options apply to every problem;
  * tally mode, precision, records and photon-id offset are fixed (field,
  * FP32, none, 0). */
@@ -262,10 +282,11 @@ int sp_mc_batch_raw_field(sp_mc_batch_t *b, int i, uint64_t *dst, int on_device,
 /* Zero every problem's tallies and photon counter. */
 int sp_mc_batch_reset(sp_mc_batch_t *b, void *stream);
 /* Autotuner: times one batched run of n_photons[] for each candidate launch
- * shape (threads per CTA 64/128/256, all or half the resident CTAs per SM,
- * compaction threshold 4/8/12/16) and for the per-problem mode, keeps the
- * fastest, stores its rate in *photons_per_s (may be NULL), then resets the
- * tallies. */
+ * shape of the one-launch mode (threads per CTA 64/128/256, all or half the
+ * resident CTAs per SM, compaction threshold 4/8/12/16, and for the
+ * streamlined kernel 8 or 16 steps per pass) and for the per-problem mode,
+ * keeps the fastest, stores its rate in *photons_per_s (may be NULL), then
+ * resets the tallies. */
 int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed,
                          double *photons_per_s, void *stream);
 void sp_mc_batch_destroy(sp_mc_batch_t *b);

@@ -35,7 +35,7 @@ NBATCH, NBIN, NHIST = 16, 64, 257
 Q32 = float(2 ** 32)
 Q16 = float(2 ** 16)
 COUNT_NAMES = ("launched", "interactions", "scatters", "rr_survive", "rr_kill",
-               "exit_R", "exit_T", "gated", "steps")
+               "exit_R", "exit_T", "gated", "steps", "solid_steps")
 EXIT_R, EXIT_T, EXIT_RR, EXIT_GATE = 1, 2, 3, 4
 
 

@@ -178,7 +178,7 @@ static void run_photon(const or_problem_t *pb, uint64_t pid, or_tallies_t *t,
     double w = 1.0, tau = -log(or_uniform(r[2]));
     double s = 0.0, P = 0.0, A = 0.0;
     uint32_t event = 1u;
-    int64_t n_int = 0, n_steps = 0, n_surv = 0;
+    int64_t n_int = 0, n_steps = 0, n_surv = 0, n_solid = 0;
     int kind = 0;
 
     t->photons[b] += 1;
@@ -234,6 +234,7 @@ static void run_photon(const or_problem_t *pb, uint64_t pid, or_tallies_t *t,
             t->depth[b][pore][(z * OR_NBIN) / nz] += qd;
             s += l;
             n_steps += 1;
+            if (!pore) n_solid += 1;
         }
         if (!pore && ev == EV_CROSS) tau -= pb->mus * l;
         for (int a = 0; a < 3; ++a) p[a] += l * u[a];
@@ -306,6 +307,7 @@ static void run_photon(const or_problem_t *pb, uint64_t pid, or_tallies_t *t,
     }
     t->A[b] += q32(A);
     t->counts[OR_C_STEPS] += (uint64_t)n_steps;
+    t->counts[OR_C_SOLID_STEPS] += (uint64_t)n_solid;
 
     if (ri) {
         ri[0] = n_int; ri[1] = n_steps; ri[2] = kind; ri[3] = n_surv;

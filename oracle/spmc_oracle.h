@@ -30,7 +30,9 @@ extern "C" {
 /* counts[] slots */
 enum {
     OR_C_LAUNCHED = 0, OR_C_INTERACT, OR_C_SCATTER, OR_C_RR_SURVIVE,
-    OR_C_RR_KILL, OR_C_EXIT_R, OR_C_EXIT_T, OR_C_GATED, OR_C_STEPS, OR_NCOUNT
+    OR_C_RR_KILL, OR_C_EXIT_R, OR_C_EXIT_T, OR_C_GATED, OR_C_STEPS,
+    OR_C_SOLID_STEPS,       /* voxel steps (l > 0) inside solid voxels       */
+    OR_NCOUNT
 };
 
 /* per-photon record exit kinds */

@@ -73,6 +73,11 @@ struct sp_mc {
     u64 n_rec = 0, iter_limit_opt = 0, pid_offset = 0;
     int compact_k = 8;
     int mirror = 0;         // lateral faces: 0 periodic, 1 mirrors
+    int variant = 1;        // FP32 kernel: 0 generic template, 1 streamlined
+    int steps_per_pass = 8; // streamlined FP32 kernel: voxel steps per warp pass
+    int l2_persist = 0;     // persisting-L2 window over the field
+    u32 bin_mul = 0;        // depth bin by multiply-high, when exact for this nz
+    int bin_exact = 0;
     // device memory
     u64 *d_bricks = nullptr, *d_field = nullptr, *d_layer = nullptr, *d_bin_count = nullptr;
     DevTallies *d_tal = nullptr;
@@ -100,6 +105,21 @@ static u64 iter_limit(const sp_mc *h) {
     const double s = path_cap(h);
     const double lim = (3.0 * 1.7320508075688772 + 4.0 * h->mus + 1.0) * s + 1.0e4;
     return lim > 4.0e9 ? 0xffffffffull : (u64)lim;
+}
+
+// Depth bin floor(64 iz / nz) as umulhi(64 iz, ceil(2^32 / nz)); used only
+// when that is exact for every layer of the volume, which is checked here.
+static void set_bin_mul(sp_mc *h) {
+    h->bin_mul = 0;
+    h->bin_exact = 0;
+    const int nz = h->nz;
+    if (nz < 2 || (u64)nz * 64 >= (1ull << 32)) return;
+    const u64 m = ((1ull << 32) + (u64)nz - 1) / (u64)nz;
+    if (m >= (1ull << 32)) return;
+    for (int z = 0; z < nz; ++z)
+        if ((int)((((u64)z * 64) * m) >> 32) != (int)(((long long)z * kNBin) / nz)) return;
+    h->bin_mul = (u32)m;
+    h->bin_exact = 1;
 }
 
 // FP32 copies of the optics and limits of a launch (computed on the host so
@@ -341,6 +361,7 @@ __global__ void finalize_kernel(const DevTallies *__restrict__ tal, const u64 *_
     out->exit_T = tal->counts[C_EXIT_T];
     out->gated_n = tal->counts[C_GATED];
     out->steps = tal->counts[C_STEPS];
+    out->solid_steps = tal->counts[C_SOLID_STEPS];
 }
 
 // Field in x-fastest order: Phi/S0 as float/double, or the raw Q32.32 words
@@ -471,6 +492,7 @@ sp_mc_t *sp_mc_create(const uint8_t *mask, int nx, int ny, int nz, double voxel_
     }
     h->n_pore = n_pore;
     h->porosity = (double)n_pore / (double)n_vox;
+    set_bin_mul(h);
 
     auto bail = [&](int code) -> sp_mc_t * {
         (void)code;
@@ -573,6 +595,15 @@ int sp_mc_set_option(sp_mc_t *h, int key, double value) {
         if (value < 0 || value > 1.8e19) return fail(SP_EINVAL, "photon id offset out of range");
         if (h->photons_done) return fail(SP_EINVAL, "the photon id offset can only be set before the first run");
         h->pid_offset = (u64)value; return SP_OK;
+    case SP_OPT_KERNEL:
+        if (value != 0 && value != 1) return fail(SP_EINVAL, "kernel variant must be 0 or 1");
+        h->variant = (int)value; return SP_OK;
+    case SP_OPT_STEPS_PER_PASS:
+        if (value < 1 || value > 64) return fail(SP_EINVAL, "steps per pass must be in [1, 64]");
+        h->steps_per_pass = (int)value; return SP_OK;
+    case SP_OPT_L2_PERSIST:
+        if (value != 0 && value != 1) return fail(SP_EINVAL, "L2 persistence must be 0 or 1");
+        h->l2_persist = (int)value; return SP_OK;
     default: return fail(SP_EINVAL, "unknown option %d", key);
     }
 }
@@ -594,8 +625,38 @@ int sp_mc_get_option(const sp_mc_t *h, int key, double *value) {
     case SP_OPT_PID_OFFSET: *value = (double)h->pid_offset; return SP_OK;
     case SP_OPT_COMPACT: *value = h->compact_k; return SP_OK;
     case SP_OPT_LATERAL_BC: *value = h->mirror; return SP_OK;
+    case SP_OPT_KERNEL: *value = h->variant; return SP_OK;
+    case SP_OPT_STEPS_PER_PASS: *value = h->steps_per_pass; return SP_OK;
+    case SP_OPT_L2_PERSIST: *value = h->l2_persist; return SP_OK;
     default: return fail(SP_EINVAL, "unknown option %d", key);
     }
+}
+
+// Persisting-L2 access-policy window over the voxel field.  The field of the
+// headline volume (256^3 x 8 B = 134 MB) is a little larger than the L2, so
+// plain replacement keeps evicting lines that the next REDs need; a
+// persisting window over the field with hitRatio = set-aside / window keeps a
+// fixed share of its lines resident.  The set-aside is a limit of this
+// process's CUDA context (cudaLimitPersistingL2CacheSize, raised here to the
+// device maximum when it is lower); it ends with the context and changes
+// nothing that outlives the process.
+static int persist_window(sp_mc *h, LaunchExtras *ex) {
+    int max_persist = 0, max_window = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, h->device));
+    if (max_persist <= 0 || max_window <= 0) return SP_OK;     // not supported: plain launch
+    size_t cur = 0;
+    CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+    if (cur < (size_t)max_persist) {
+        CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist));
+        CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+    }
+    const size_t bytes = std::min<size_t>(h->n_field * sizeof(u64), (size_t)max_window);
+    if (!cur || !bytes) return SP_OK;
+    ex->window = h->d_field;
+    ex->window_bytes = bytes;
+    ex->hit_ratio = (float)std::min(1.0, (double)cur / (double)bytes);
+    return SP_OK;
 }
 
 // One single-problem transport launch of n_photons from photon id pid_begin
@@ -611,14 +672,15 @@ static int launch_run(sp_mc *h, u64 n_photons, u64 seed, u64 pid_begin, const u6
     const bool f64 = h->precision == 64;
     const bool field = h->field != 0;
     if (smem > 48 * 1024) {
-        CUDA_TRY(cudaFuncSetAttribute(f64 ? kernel_f64(field, h->mirror != 0) : kernel_f32(field, h->mirror != 0),
+        CUDA_TRY(cudaFuncSetAttribute(f64 ? kernel_f64(field, h->mirror != 0)
+                                          : kernel_f32(field, h->mirror != 0, h->variant),
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     int blocks = h->blocks_opt;
     if (blocks <= 0) {
         int per_sm = 0;
         CUDA_TRY(f64 ? occupancy_f64(field, h->mirror != 0, h->threads, smem, &per_sm)
-                     : occupancy_f32(field, h->mirror != 0, h->threads, smem, &per_sm));
+                     : occupancy_f32(field, h->mirror != 0, h->variant, h->threads, smem, &per_sm));
         if (per_sm < 1) return fail(SP_ECUDA, "transport kernel cannot be resident with %zu B smem", smem);
         blocks = per_sm * h->sm_count;
     }
@@ -647,11 +709,20 @@ static int launch_run(sp_mc *h, u64 n_photons, u64 seed, u64 pid_begin, const u6
     p.iter_limit = iter_limit(h);
     p.compact_k = h->compact_k;
     p.mirror = h->mirror;
+    p.steps_per_pass = h->steps_per_pass;
+    p.bin_mul = h->bin_mul;
+    p.bin_exact = h->bin_exact;
     fill_f32(h, p.s_max, p.f32, p.hg_iso, p.small_x);
 
+    LaunchExtras ex;
+    ex.variant = h->variant;
+    if (!f64 && field && h->l2_persist) {
+        const int rc = persist_window(h, &ex);
+        if (rc) return rc;
+    }
     CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
     CUDA_TRY(f64 ? launch_transport_f64(p, field, blocks, h->threads, smem, s)
-                 : launch_transport_f32(p, field, blocks, h->threads, smem, s));
+                 : launch_transport_f32(p, field, blocks, h->threads, smem, s, ex));
     return SP_OK;
 }
 
@@ -930,8 +1001,9 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     tmp.nx = nx; tmp.ny = ny; tmp.nz = nz;
     tmp.mus = mu_s * voxel_h; tmp.mua = mu_a * voxel_h; tmp.g = g;
     tmp.porosity = porosity;
+    set_bin_mul(&tmp);
     int per_sm = 0;
-    if (occupancy_f32(false, false, tmp.threads, 0, &per_sm) != cudaSuccess || per_sm < 1)
+    if (occupancy_f32(false, false, tmp.variant, tmp.threads, 0, &per_sm) != cudaSuccess || per_sm < 1)
         return fail(SP_ECUDA, "CUDA error");
 
     TransportParams p{};
@@ -952,9 +1024,14 @@ extern "C" int sp_mc_simulate_noalloc(const uint8_t *d_mask, int nx, int ny, int
     p.iter_limit = iter_limit(&tmp);
     p.compact_k = tmp.compact_k;
     p.mirror = 0;
+    p.steps_per_pass = tmp.steps_per_pass;
+    p.bin_mul = tmp.bin_mul;
+    p.bin_exact = tmp.bin_exact;
     fill_f32(&tmp, p.s_max, p.f32, p.hg_iso, p.small_x);
+    LaunchExtras ex;
+    ex.variant = tmp.variant;
 
-    if (n_photons > 0 && launch_transport_f32(p, false, per_sm * sms, tmp.threads, 0, s) != cudaSuccess)
+    if (n_photons > 0 && launch_transport_f32(p, false, per_sm * sms, tmp.threads, 0, s, ex) != cudaSuccess)
         return fail(SP_ECUDA, "CUDA error");
     finalize_kernel<<<1, kNBin, 0, s>>>(tal, nullptr, bin_count, nx, ny, nz, porosity, d_result);
     u32 flags = 0;
@@ -994,12 +1071,17 @@ struct sp_mc_batch {
     BatchProblem *d_table = nullptr;
     u64 *d_next = nullptr;
     int threads = 128, blocks_per_sm = 0, compact_k = 8, use_graph = 1, mode = 0;
+    int variant = 1, steps_per_pass = 8;   // one-launch kernel and its steps per pass
+    u32 chunk = 2048;                      // photons per warp claim (streamlined kernel)
+    u64 total_chunks = 0;
+    bool any_mirror = false;
     bool table_valid = false;              // device table matches table[]
     std::vector<u64> cfg_n;                // configuration of the device table / graph
     u64 cfg_seed = 0;
     cudaStream_t cap = nullptr;            // private stream for graph capture
     cudaGraphExec_t exec = nullptr;
-    int graph_threads = 0, graph_blocks = 0, graph_compact = 0, graph_mode = 0;
+    int graph_threads = 0, graph_blocks = 0, graph_compact = 0, graph_mode = 0, graph_variant = 0,
+        graph_spp = 0;
     // per-problem mode: launches fork over side streams so one problem's tail
     // overlaps the next problem's start (graph branches when captured)
     static constexpr int kSide = 4;
@@ -1083,6 +1165,20 @@ extern "C" int sp_mc_batch_set_option(sp_mc_batch_t *b, int key, double value) {
     case SP_OPT_BATCH_MODE:
         if (value != 0 && value != 1) return fail(SP_EINVAL, "batch mode must be 0 or 1");
         b->mode = (int)value; return SP_OK;
+    case SP_OPT_KERNEL:
+    case SP_OPT_STEPS_PER_PASS: {
+        // the one-launch kernel's own setting, and every problem's for mode 1
+        if (key == SP_OPT_KERNEL && value != 0 && value != 1)
+            return fail(SP_EINVAL, "kernel variant must be 0 or 1");
+        if (key == SP_OPT_STEPS_PER_PASS && (value < 1 || value > 64))
+            return fail(SP_EINVAL, "steps per pass must be in [1, 64]");
+        if (key == SP_OPT_KERNEL) b->variant = (int)value; else b->steps_per_pass = (int)value;
+        for (sp_mc *h : b->h) {
+            const int rc = sp_mc_set_option(h, key, value);
+            if (rc) return rc;
+        }
+        return SP_OK;
+    }
     default: {
         // optics-independent per-problem options apply to every problem
         if (key == SP_OPT_TALLY_FIELD || key == SP_OPT_PRECISION || key == SP_OPT_RECORDS ||
@@ -1106,6 +1202,8 @@ extern "C" int sp_mc_batch_get_option(const sp_mc_batch_t *b, int key, double *v
     case SP_OPT_COMPACT: *value = b->compact_k; return SP_OK;
     case SP_OPT_GRAPH: *value = b->use_graph; return SP_OK;
     case SP_OPT_BATCH_MODE: *value = b->mode; return SP_OK;
+    case SP_OPT_KERNEL: *value = b->variant; return SP_OK;
+    case SP_OPT_STEPS_PER_PASS: *value = b->steps_per_pass; return SP_OK;
     default: return sp_mc_get_option(b->h[0], key, value);
     }
 }
@@ -1144,32 +1242,44 @@ static int batch_launch(sp_mc_batch *b, u64 total, cudaStream_t s) {
         return SP_OK;
     }
     int per_sm = 0;
-    CUDA_TRY(occupancy_batch(b->threads, &per_sm));
+    CUDA_TRY(occupancy_batch(b->variant, b->any_mirror, b->threads, &per_sm));
     if (per_sm < 1) return fail(SP_ECUDA, "batched transport cannot be resident with %d threads", b->threads);
     if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
     BatchParams bp{};
     bp.problems = b->d_table;
     bp.n_problems = b->n;
     bp.total_photons = total;
+    bp.total_chunks = b->total_chunks;
+    bp.chunk = b->chunk;
     bp.next = b->d_next;
     bp.key0 = (u32)b->cfg_seed;
     bp.key1 = (u32)(b->cfg_seed >> 32);
     bp.compact_k = b->compact_k;
+    bp.steps_per_pass = b->steps_per_pass;
     CUDA_TRY(cudaMemsetAsync(b->d_next, 0, sizeof(u64), s));
-    CUDA_TRY(launch_transport_batch(bp, per_sm * b->sm_count, b->threads, s));
+    CUDA_TRY(launch_transport_batch(bp, b->variant, b->any_mirror, per_sm * b->sm_count, b->threads, s));
     batch_advance_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_table, b->n);
     CUDA_TRY(cudaGetLastError());
     b->graph_threads = b->threads;
     b->graph_blocks = per_sm;
     b->graph_compact = b->compact_k;
+    b->graph_variant = b->variant;
+    b->graph_spp = b->steps_per_pass;
     b->graph_mode = 0;
     return SP_OK;
+}
+
+// Whether any problem has mirror lateral faces (selects the batched kernel).
+static void refresh_mirror(sp_mc_batch *b) {
+    b->any_mirror = false;
+    for (const sp_mc *h : b->h) b->any_mirror = b->any_mirror || h->mirror != 0;
 }
 
 extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint64_t seed,
                                void *stream) {
     if (!b || !n_photons) return fail(SP_EINVAL, "null argument");
     DeviceGuard guard(b->device);
+    refresh_mirror(b);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     u64 total = 0;
     for (int i = 0; i < b->n; ++i) total += n_photons[i];
@@ -1182,7 +1292,7 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
     const bool same_cfg = b->table_valid && want == b->cfg_n && seed == b->cfg_seed;
     if (!same_cfg) {
         // (re)build the device table from the handles' photon counters
-        u64 offset = 0;
+        u64 offset = 0, chunk_begin = 0;
         for (int i = 0; i < b->n; ++i) {
             sp_mc *h = b->h[i];
             BatchProblem &t = b->table[i];
@@ -1196,6 +1306,8 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
             t.n_photons = n_photons[i];
             t.offset = offset;
             offset += n_photons[i];
+            t.chunk_begin = chunk_begin;
+            chunk_begin += (n_photons[i] + b->chunk - 1) / b->chunk;
             const u64 lim = iter_limit(h);
             t.iter_limit = lim > 0xffffffffull ? 0xffffffffu : (u32)lim;
             fill_f32(h, path_cap(h), t.f32, t.hg_iso, t.small_x);
@@ -1205,6 +1317,7 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
         CUDA_TRY(cudaMemcpyAsync(b->d_table, b->table.data(), b->n * sizeof(BatchProblem),
                                  cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaStreamSynchronize(s));     // the host table may change after return
+        b->total_chunks = chunk_begin;
         b->cfg_n = want;
         b->cfg_seed = seed;
         b->table_valid = true;
@@ -1212,11 +1325,13 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
     }
     if (b->use_graph) {
         int per_sm = 0;
-        CUDA_TRY(occupancy_batch(b->threads, &per_sm));
+        CUDA_TRY(occupancy_batch(b->variant, b->any_mirror, b->threads, &per_sm));
         if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
         if (b->exec && (b->graph_mode != b->mode ||
                         (b->mode == 0 && (b->graph_threads != b->threads || b->graph_blocks != per_sm ||
-                                          b->graph_compact != b->compact_k)))) {
+                                          b->graph_compact != b->compact_k ||
+                                          b->graph_variant != b->variant ||
+                                          b->graph_spp != b->steps_per_pass)))) {
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
         }
@@ -1267,6 +1382,7 @@ extern "C" int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons,
                                     double *photons_per_s, void *stream) {
     if (!b || !n_photons) return fail(SP_EINVAL, "null argument");
     DeviceGuard guard(b->device);
+    refresh_mirror(b);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int saved_graph = b->use_graph;
     b->use_graph = 0;
@@ -1276,30 +1392,38 @@ extern "C" int sp_mc_batch_autotune(sp_mc_batch_t *b, const uint64_t *n_photons,
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    // one-launch candidates: threads per CTA, all or half the resident CTAs,
+    // compaction threshold and (streamlined kernel) steps per pass
     const int threads_c[] = {64, 128, 256};
     const int compact_c[] = {4, 8, 12, 16};
+    const int spp_c[] = {8, 16};
     double best = -1.0;
     int best_t = b->threads, best_b = b->blocks_per_sm, best_k = b->compact_k, best_mode = 0;
+    int best_spp = b->steps_per_pass;
     b->mode = 0;
     int rc = SP_OK;
     for (int t : threads_c) {
         int per_sm = 0;
-        if (occupancy_batch(t, &per_sm) != cudaSuccess || per_sm < 1) continue;
+        if (occupancy_batch(b->variant, b->any_mirror, t, &per_sm) != cudaSuccess || per_sm < 1) continue;
         for (int bps : {per_sm, (per_sm + 1) / 2}) {
             for (int k : compact_c) {
-                b->threads = t;
-                b->blocks_per_sm = bps;
-                b->compact_k = k;
-                cudaEventRecord(e0, s);
-                if ((rc = sp_mc_batch_run(b, n_photons, seed, stream)) != SP_OK) goto done;
-                cudaEventRecord(e1, s);
-                float ms = 0;
-                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    rc = fail(SP_ECUDA, "autotune timing failed");
-                    goto done;
+                for (int spp : spp_c) {
+                    if (b->variant == 0 && spp != spp_c[0]) continue;
+                    b->threads = t;
+                    b->blocks_per_sm = bps;
+                    b->compact_k = k;
+                    b->steps_per_pass = spp;
+                    cudaEventRecord(e0, s);
+                    if ((rc = sp_mc_batch_run(b, n_photons, seed, stream)) != SP_OK) goto done;
+                    cudaEventRecord(e1, s);
+                    float ms = 0;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        rc = fail(SP_ECUDA, "autotune timing failed");
+                        goto done;
+                    }
+                    const double rate = (double)total / (ms * 1e-3);
+                    if (rate > best) { best = rate; best_t = t; best_b = bps; best_k = k; best_spp = spp; }
                 }
-                const double rate = (double)total / (ms * 1e-3);
-                if (rate > best) { best = rate; best_t = t; best_b = bps; best_k = k; }
             }
         }
     }
@@ -1323,6 +1447,7 @@ done:
     b->threads = best_t;
     b->blocks_per_sm = best_b;
     b->compact_k = best_k;
+    b->steps_per_pass = best_spp;
     b->mode = best_mode;
     b->use_graph = saved_graph;
     if (rc) return rc;

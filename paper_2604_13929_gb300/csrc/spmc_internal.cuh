@@ -20,7 +20,7 @@ constexpr int kNHist = 257;   // pore-path histogram, 256 bins on [0, 4 nz) + ov
 enum { B_R = 0, B_T, B_A, B_GATED, B_LOST, B_GAIN, B_PHOTONS, B_N = 8 };
 // Integer event counts.
 enum { C_LAUNCHED = 0, C_INTERACT, C_SCATTER, C_RR_SURV, C_RR_KILL, C_EXIT_R, C_EXIT_T,
-       C_GATED, C_STEPS, C_N = 16 };
+       C_GATED, C_STEPS, C_SOLID_STEPS, C_N = 16 };
 // Error flags raised by kernels.
 enum { F_ITER_LIMIT = 1u, F_OVERFLOW = 2u };
 
@@ -61,6 +61,9 @@ struct TransportParams {
     int hg_iso;                    // |g| < 1e-6: isotropic scattering
     int mirror;                    // lateral faces: 0 periodic, 1 specular mirrors
     int small_x;                   // mu_a * sqrt(3) <= 0.1: Taylor branch for 1 - exp(-x)
+    int steps_per_pass;            // FP32 kernel: voxel steps per pass of the warp
+    u32 bin_mul;                   // depth bin = umulhi(64 iz, bin_mul) when bin_exact
+    int bin_exact;
     // The optics again as FP32, converted on the host: in FP32 kernels every
     // constant is a float, so no double-to-float conversion (an FP64-pipe
     // instruction) is ever rematerialised inside the loop.
@@ -74,12 +77,16 @@ struct TransportParams {
 // tallies, dimensions and FP32 optics.  Photons of all problems share one
 // claim counter: global index k belongs to the problem whose
 // [offset, offset + n_photons) contains it, with photon id pid_begin + k - offset.
+// The streamlined FP32 kernel claims work in chunks of `chunk` photons of one
+// problem per warp: problem i owns the global chunk indices
+// [chunk_begin, chunk_begin + ceil(n_photons / chunk)).
 struct BatchProblem {
     const u64 *bricks;
     u64 *field;
     DevTallies *tal;
     int nx, ny, nz, nbx, nby, nbz;
     u64 pid_begin, n_photons, offset;
+    u64 chunk_begin;
     u32 iter_limit;
     int hg_iso, small_x, mirror;
     TransportParams::F32 f32;
@@ -89,21 +96,35 @@ struct BatchParams {
     const BatchProblem *problems;   // device table
     int n_problems;
     u64 total_photons;              // sum of n_photons (one run)
+    u64 total_chunks;               // chunks over all problems (streamlined kernel)
+    u32 chunk;                      // photons per chunk (streamlined kernel)
     u64 *next;                      // claim counter, zeroed before each launch
     u32 key0, key1;                 // Philox key = seed (shared by all problems)
     int compact_k;
+    int steps_per_pass;
+};
+
+// Launch choices of the FP32 path beyond TransportParams: which kernel, and
+// an optional L2 access-policy window (persisting lines) over the field.
+struct LaunchExtras {
+    int variant = 1;               // 0 generic template kernel, 1 streamlined FP32 kernel
+    void *window = nullptr;        // base of the persisting window (nullptr: none)
+    size_t window_bytes = 0;
+    float hit_ratio = 0.0f;
 };
 
 // Launch helpers (defined in the per-precision translation units).
 cudaError_t launch_transport_f32(const TransportParams &p, bool field, int blocks, int threads,
-                                 size_t smem, cudaStream_t s);
+                                 size_t smem, cudaStream_t s, const LaunchExtras &e);
 cudaError_t launch_transport_f64(const TransportParams &p, bool field, int blocks, int threads,
                                  size_t smem, cudaStream_t s);
-cudaError_t occupancy_f32(bool field, bool mirror, int threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_transport_batch(const BatchParams &b, int blocks, int threads, cudaStream_t s);
-cudaError_t occupancy_batch(int threads, int *blocks_per_sm);
+cudaError_t occupancy_f32(bool field, bool mirror, int variant, int threads, size_t smem,
+                          int *blocks_per_sm);
+cudaError_t launch_transport_batch(const BatchParams &b, int variant, bool mirror, int blocks,
+                                   int threads, cudaStream_t s);
+cudaError_t occupancy_batch(int variant, bool mirror, int threads, int *blocks_per_sm);
 cudaError_t occupancy_f64(bool field, bool mirror, int threads, size_t smem, int *blocks_per_sm);
-const void *kernel_f32(bool field, bool mirror);
+const void *kernel_f32(bool field, bool mirror, int variant);
 const void *kernel_f64(bool field, bool mirror);
 
 }  // namespace spmc

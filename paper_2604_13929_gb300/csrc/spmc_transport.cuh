@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256, kBatch ? 3 : SPMC_MIN_BLOCKS) transport_k
     u64 word = 0;                                // mask bits of the current brick
     Real ux = 0, uy = 0, uz = 1;
     Real w = 1, tau = 0, s = 0, P = 0, A = 0;
-    u32 event = 1, n_int = 0, n_surv = 0, n_scat = 0, n_steps = 0, iters = 0;
+    u32 event = 1, n_int = 0, n_surv = 0, n_scat = 0, n_steps = 0, n_solid = 0, iters = 0;
     // FP32 traversal: face parameters along the current ray, origin fractions
     Real tmx = kInf, tmy = kInf, tmz = 1, dtx = kInf, dty = kInf, dtz = 1, t = 0;
     Real fx = 0, fy = 0, fz = 0;
@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(256, kBatch ? 3 : SPMC_MIN_BLOCKS) transport_k
         atomicAdd(&tc[C_SCATTER], (u64)n_scat);
         atomicAdd(&tc[C_RR_SURV], (u64)n_surv);
         atomicAdd(&tc[C_STEPS], (u64)n_steps);
+        atomicAdd(&tc[C_SOLID_STEPS], (u64)n_solid);
         if (pid - p.rec_base < p.n_rec) {
             long long *ri = p.rec_ints + (pid - p.rec_base) * 4;
             double *rv = p.rec_vals + (pid - p.rec_base) * 4;
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(256, kBatch ? 3 : SPMC_MIN_BLOCKS) transport_k
             }
             s += seg;
             ++n_steps;
+            n_solid += pore ? 0u : 1u;
         }
         if (ev == 0) tau -= need;
         if constexpr (kExact) {
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(256, kBatch ? 3 : SPMC_MIN_BLOCKS) transport_k
                         tmx = kInf; tmy = kInf; dtx = kInf; dty = kInf; tmz = 1; dtz = 1; t = 0;
                     }
                     w = 1; tau = O::neg_log(O::uniform(r[2])); s = 0; P = 0; A = 0;
-                    event = 1; n_int = 0; n_surv = 0; n_scat = 0; n_steps = 0; iters = 0;
+                    event = 1; n_int = 0; n_surv = 0; n_scat = 0; n_steps = 0; n_solid = 0; iters = 0;
                     batch = (int)(pid & (kNBatch - 1));
                     brick = brick_of(ix, iy, 0);
                     bit = bit_of(ix, iy, 0);

@@ -28,7 +28,8 @@ SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_ESTEPLIMIT, SP_EOVERFLOW = 0, -1, -2, 
 NBATCH, NBIN, NHIST = 16, 64, 257
 OPT = {"path_cap": 1, "rr_weight": 2, "rr_mult": 3, "tally_field": 4, "precision": 5,
        "records": 6, "blocks": 7, "threads": 8, "iter_limit": 9, "smem_bricks": 10,
-       "pid_offset": 11, "compact": 12, "graph": 13, "lateral_bc": 14, "batch_mode": 15}
+       "pid_offset": 11, "compact": 12, "graph": 13, "lateral_bc": 14, "batch_mode": 15,
+       "kernel": 16, "steps_per_pass": 17, "l2_persist": 18}
 ERR_NAMES = {SP_EINVAL: "SP_EINVAL", SP_ENOMEM: "SP_ENOMEM", SP_ECUDA: "SP_ECUDA",
              SP_ESTEPLIMIT: "SP_ESTEPLIMIT", SP_EOVERFLOW: "SP_EOVERFLOW"}
 
@@ -49,7 +50,7 @@ class Result(ctypes.Structure):
         ("p_pore_gt_L", _D), ("pore_hist", _D * NHIST),
         ("launched", _U64), ("interactions", _U64), ("scatters", _U64),
         ("rr_survive", _U64), ("rr_kill", _U64), ("exit_R", _U64), ("exit_T", _U64),
-        ("gated_n", _U64), ("steps", _U64),
+        ("gated_n", _U64), ("steps", _U64), ("solid_steps", _U64),
         ("raw_R", _U64 * NBATCH), ("raw_T", _U64 * NBATCH), ("raw_A", _U64 * NBATCH),
         ("raw_gated", _U64 * NBATCH), ("raw_lost", _U64 * NBATCH), ("raw_gain", _U64 * NBATCH),
         ("batch_photons", _U64 * NBATCH),

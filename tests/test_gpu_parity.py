@@ -96,7 +96,7 @@ def test_c1_same_streams_fp32(spmc, c1_mask):
     for k in ("R", "T", "A"):
         assert abs(g[k] - o[k]) < 2e-4, k
     assert g["launched"] == n
-    for k in ("interactions", "exit_R", "exit_T", "rr_kill", "gated"):
+    for k in ("interactions", "exit_R", "exit_T", "rr_kill", "gated", "steps", "solid_steps"):
         ok = o["counts"][k] if k != "gated" else o["counts"]["gated"]
         gk = g[k] if k != "gated" else g["gated_n"]
         assert abs(gk - ok) <= max(3, 1e-3 * ok), (k, gk, ok)
@@ -202,7 +202,7 @@ def test_fp64_transport_exact_on_interface_free_geometry(spmc, pattern):
     o = orc.run(mask, 0.6, 0.03, 0.7, n, 99, n_rec=n)
     assert np.array_equal(gi, o["rec_ints"])
     for k in ("launched", "interactions", "scatters", "rr_survive", "rr_kill", "exit_R",
-              "exit_T", "steps"):
+              "exit_T", "steps", "solid_steps"):
         assert g[k] == o["counts"][k], k
     assert g["gated_n"] == o["counts"]["gated"]
     for k in ("R", "T", "A", "gated", "lost", "gain"):
@@ -246,8 +246,10 @@ def test_all_pore_unit_fluence_exact(spmc):
 @pytest.mark.parametrize("precision", [32, 64])
 def test_pore_path_moments_straight_rays(spmc, precision):
     """mu_s = 0 through laterally uniform layers: every photon has P = n_p and
-    w = exp(-mu_a n_s); the exit-weighted moments match the oracle's sums
-    (each photon one Q32.32 / Q48.16 rounding, so within N units)."""
+    w = exp(-mu_a n_s); the exit-weighted moments match the oracle's sums.
+    FP64 transport: each photon one Q32.32 / Q48.16 rounding, so within N
+    units.  FP32: the weight after n_s decays carries FP32 rounding (about
+    n_s ulp), so within 1e-6 relative."""
     pattern = [1, 0, 1, 1, 0, 0, 1, 1, 1, 0, 1]
     mask = inputs.layered(pattern, 3, 4)
     n, n_p = 20000, pattern.count(1)
@@ -257,7 +259,8 @@ def test_pore_path_moments_straight_rays(spmc, precision):
     sim.close()
     o = orc.run(mask, 0.0, 0.3, 0.7, n, 8)
     for k in ("sum_w", "sum_wP", "sum_wP2"):
-        assert abs(_u128(t["raw_" + k]) - o[k]) <= n, k
+        tol = n if precision == 64 else 1e-6 * o[k]
+        assert abs(_u128(t["raw_" + k]) - o[k]) <= tol, (k, _u128(t["raw_" + k]), o[k])
     assert abs(t["pore_path_mean"] - n_p) < 1e-6
     assert abs(t["pore_path_m2"] - n_p ** 2) < 1e-4
 
@@ -308,7 +311,9 @@ def test_bitwise_determinism_across_runs_configs_and_splits(spmc, c1_mask):
 
     base_t, base_f = run()
     for opt in ({}, {"threads": 128}, {"blocks": 37, "threads": 64}, {"split": True},
-                {"smem_bricks": 2048}, {"compact": 1}, {"compact": 32}):
+                {"smem_bricks": 2048}, {"compact": 1}, {"compact": 32},
+                {"steps_per_pass": 1}, {"steps_per_pass": 29, "compact": 5},
+                {"l2_persist": 1}):
         t, f = run(**opt)
         assert np.array_equal(f, base_f), opt
         for k in ("raw_R", "raw_T", "raw_A", "raw_gated", "raw_lost", "raw_gain", "raw_hist",
@@ -354,7 +359,7 @@ def test_ragged_and_degenerate_shapes(spmc, shape):
     sim.run(n, 2)
     g = sim.tallies()
     o = orc.run(mask, 0.6, 0.03, 0.5, n, 2)
-    for k in ("launched", "interactions", "exit_R", "exit_T", "rr_kill"):
+    for k in ("launched", "interactions", "exit_R", "exit_T", "rr_kill", "steps", "solid_steps"):
         assert g[k] == o["counts"][k], (shape, k)
     assert abs(g["closure"] - 1) < 1e-9
     sim.close()
@@ -452,7 +457,7 @@ def test_c2_same_streams_against_oracle(spmc, c2_mask):
               "pore_path_m2", "escape_weight"):
         assert abs(g[k] / o[k] - 1) < 2e-3, (k, g[k], o[k])
     assert abs(g["p_pore_gt_L"] - o["p_pore_gt_L"]) < 2e-3
-    for k in ("interactions", "scatters", "exit_R", "exit_T", "rr_kill", "steps"):
+    for k in ("interactions", "scatters", "exit_R", "exit_T", "rr_kill", "steps", "solid_steps"):
         assert abs(g[k] - o["counts"][k]) <= max(3, 1e-3 * o["counts"][k]), (k, g[k], o["counts"][k])
     assert abs(g["closure"] - 1) < 1e-6 and abs(g["identity_residual"]) < 1e-12
 
@@ -463,7 +468,11 @@ def test_512_cubed_high_photon_ids_match_oracle(spmc):
     high word of the Philox counter, the brick and field indexing over the
     whole volume and the record offsets must all agree with the oracle on the
     same ids.  The mask tiles a periodic 64^3 Cahn-Hilliard field 8 x 8 x 8
-    (seamless, porosity 0.90)."""
+    (seamless, porosity 0.90).  Bounds: the first 8 sites of >= 99.9 % of
+    photons (FP64) and >= 99 % (FP32); whole FP64 histories >= 90 % and
+    aggregate counts within 1 %, as for the oracle against itself with
+    one-ulp transcendental differences over these ~1600-step histories
+    (tests/test_oracle_sensitivity.py: 92 % identical, counts within 0.5 %)."""
     tile = inputs.spinodal_mask(64, 0.90, 1000, seed=3, device="cuda")
     mask = np.ascontiguousarray(np.tile(tile, (8, 8, 8)))
     n = 10000
@@ -481,10 +490,10 @@ def test_512_cubed_high_photon_ids_match_oracle(spmc):
         same = np.all(gi == o["rec_ints"], axis=1)
         res[prec] = (ok.mean(), same.mean(), t)
         assert t["launched"] == n and t["depth_count"].sum() == 512 ** 3
-    assert res[64][0] >= 0.999 and res[64][1] >= 0.999, res[64][:2]
+    assert res[64][0] >= 0.999 and res[64][1] >= 0.90, res[64][:2]
     assert res[32][0] >= 0.99, res[32][:2]
-    for k in ("interactions", "exit_R", "exit_T", "rr_kill", "steps"):
-        assert abs(res[64][2][k] - o["counts"][k]) <= max(2, 1e-3 * o["counts"][k]), k
+    for k in ("interactions", "exit_R", "exit_T", "rr_kill", "steps", "solid_steps"):
+        assert abs(res[64][2][k] - o["counts"][k]) <= max(10, 1e-2 * o["counts"][k]), k
         assert abs(res[32][2][k] - o["counts"][k]) <= max(10, 1e-2 * o["counts"][k]), k
 
 

@@ -155,6 +155,7 @@ def test_pure_absorption_slab_transmits_exp_minus_mua_L():
     expect = np.exp(-mua * z) * (1 - math.exp(-mua)) / mua
     assert np.allclose(layer, expect, rtol=1e-9, atol=0)
     assert res["counts"]["steps"] == 5000 * nz
+    assert res["counts"]["solid_steps"] == 5000 * nz
 
 
 def test_all_pore_mask_gives_unit_transmission_and_fluence():
@@ -172,6 +173,7 @@ def test_all_pore_mask_gives_unit_transmission_and_fluence():
     h = res["hist"]
     assert h[64] == 4000 * 2 ** 32 and h.sum() == h[64]
     assert res["counts"]["interactions"] == 0
+    assert res["counts"]["steps"] == 4000 * nz and res["counts"]["solid_steps"] == 0
 
 
 def test_pore_path_moments_of_straight_rays():
@@ -242,6 +244,7 @@ def test_pure_absorption_through_mask_brute_force():
     iy = np.floor(philox_ref.uniform(w0[1]) * ny).astype(int)
     field = np.zeros((nz, ny, nx))
     T = 0.0
+    solid = 0
     e1 = math.exp(-mua)
     for x, y in zip(ix, iy):
         w = 1.0
@@ -251,7 +254,9 @@ def test_pure_absorption_through_mask_brute_force():
             else:
                 field[z, y, x] += w * (1 - e1) / mua
                 w *= e1
+                solid += 1
         T += w
+    assert res["counts"]["steps"] == N * nz and res["counts"]["solid_steps"] == solid
     n = orc.normalise(res)
     assert abs(n["T"] - T / N) < 1e-9
     assert np.allclose(res["field"].astype(np.float64) / Q32, field, rtol=1e-9, atol=N * 2.0 ** -32)

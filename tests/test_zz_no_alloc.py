@@ -19,7 +19,7 @@ MUS, MUA, G = 0.5, 0.005, 0.7
 RAW = ("raw_R", "raw_T", "raw_A", "raw_gated", "raw_lost", "raw_gain", "batch_photons",
        "raw_depth", "raw_hist", "raw_sum_w", "raw_sum_wP", "raw_sum_wP2")
 COUNTS = ("launched", "interactions", "scatters", "rr_survive", "rr_kill", "exit_R", "exit_T",
-          "gated_n", "steps")
+          "gated_n", "steps", "solid_steps")
 FLOATS = ("R", "T", "A", "gated", "lost", "gain", "closure", "phi_3d", "phi_1d", "phi_pore",
           "r", "ratio", "porosity", "s_max", "escape_weight", "pore_path_mean")
 
