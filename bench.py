@@ -149,6 +149,24 @@ def make_mask(device):
     return make_masks(device)[0]
 
 
+def profile_mode(spmc, torch, stream, mask, photons):
+    """The headline workload in the depth-profile tally mode (per-phase depth
+    bins staged in shared memory instead of the 134 MB voxel field): every
+    estimator of the bench line except the voxel field itself."""
+    sim = spmc.Simulation(mask, MUS, MUA, G, tally_field=0)
+    sim.run(photons // 10, SEED + 1, stream)
+    sim.reset(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.run(photons, SEED, stream)
+    e1.record(stream)
+    t = sim.tallies(stream)
+    sim.close()
+    sec = e0.elapsed_time(e1) / 1e3
+    return {"photons": photons, "photons_per_s": photons / sec, "voxel_steps_per_s": t["steps"] / sec,
+            **{k: t[k] for k in ("R", "T", "A", "phi_3d", "r", "ratio")}}
+
+
 def other_workloads(spmc, torch, stream, m70, photons):
     """256^3 phi = 0.70 (same Cahn-Hilliard field) and homogeneous 256^3 slabs
     at the optics matched to phi = 0.90 and 0.70 (mu h (1 - phi), Eq.
@@ -441,7 +459,9 @@ def surrogate_bench(torch, args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     t0 = time.perf_counter()
     train_set = sg.make_fields(args.surrogate_train, seed=1, photons=args.surrogate_photons, n=n)
-    test_set = sg.make_fields(args.surrogate_test, seed=2, photons=args.surrogate_photons, n=n)
+    # held-out masks are judged against a Monte Carlo reference of many more
+    # photons than a training field, so its own noise is negligible
+    test_set = sg.make_fields(args.surrogate_test, seed=2, photons=args.surrogate_ref_photons, n=n)
     data_s = time.perf_counter() - t0
     net = spnn.UNet(c0, n, batch)
     net.set_params(spnn.init_params(c0, 7))
@@ -459,9 +479,12 @@ def surrogate_bench(torch, args):
     for name, kind, ci, co in spnn.layer_table(c0):
         v = (n >> lv[name[:2]]) ** 3
         fl += 2 * v * ci * co * {"conv3": 27, "down": 1, "up": 8}[kind]
-    mc_rate = test_set.info["mc_fields_per_s"]
+    # Monte Carlo fields/s: the engine producing one 64^3 field at the
+    # training photon count (1e7), from the training set's measured rate
+    mc_photons_per_s = train_set.info["mc_photons_per_s"]
+    mc_rate = mc_photons_per_s / args.surrogate_photons
     # Monte Carlo given the surrogate's time per field: its profile error on the held-out masks
-    eq_photons = max(1000, int(test_set.info["mc_photons_per_s"] / rate["fields_per_s"]))
+    eq_photons = max(1000, int(mc_photons_per_s / rate["fields_per_s"]))
     eq_target, _ = sg.simulate(test_set.mask, test_set.optics, eq_photons, seed=sg.MC_SEED + 99)
     eq_rms = sg.profile_rms(sg.profiles(eq_target, test_set.mask), sg.profiles(test_set.target, test_set.mask))
     eq_d = (eq_target - test_set.target).double()
@@ -472,8 +495,10 @@ def surrogate_bench(torch, args):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"3D U-Net c0={c0} (4 levels, 32-256 channels) on {n}^3 Cahn-Hilliard masks, "
                                    f"porosity U[0.5,0.95], mu_s h logU[0.1,2], mu_a h U[0.001,0.05], "
-                                   f"g U[0,0.9]; {args.surrogate_train} training / {args.surrogate_test} held-out "
-                                   f"Monte Carlo fields of {args.surrogate_photons:.0e} photons; batch {batch}",
+                                   f"g U[0,0.9]; {args.surrogate_train} training fields of "
+                                   f"{args.surrogate_photons:.0e} photons, {args.surrogate_test} held-out masks "
+                                   f"judged against {args.surrogate_ref_photons:.0e}-photon Monte Carlo; "
+                                   f"batch {batch}",
                        "params": net.param_count},
             "mc_fields_per_s": mc_rate, "speedup_vs_mc": rate["fields_per_s"] / mc_rate,
             "heldout": ev,
@@ -487,7 +512,7 @@ def surrogate_bench(torch, args):
                          "tflops": 3 * fl * batch * args.surrogate_steps / train_s / 1e12,
                          "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-10:])),
                          "log": log[::max(1, len(log) // 12)]},
-            "data_seconds": data_s, "mc_photons_per_s": test_set.info["mc_photons_per_s"],
+            "data_seconds": data_s, "mc_photons_per_s": mc_photons_per_s,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
                          "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"], "traffic": None,
                          "kernel": "spnn rows_kernel, all 20 forward layers", "flop_per_field": fl,
@@ -546,11 +571,13 @@ def main():
                     help="c2: the 256^3 phi=0.90 headline; batch: 64 masks of uneven size "
                          "(64^3..256^3) and optics, 1e7 photons each, one launch per step")
     ap.add_argument("--precision-photons", type=int, default=1_000_000_000)
-    ap.add_argument("--surrogate-train", type=int, default=4096)
+    ap.add_argument("--surrogate-train", type=int, default=8192)
     ap.add_argument("--surrogate-test", type=int, default=128)
     ap.add_argument("--surrogate-steps", type=int, default=3000)
     ap.add_argument("--surrogate-batch", type=int, default=256)
     ap.add_argument("--surrogate-photons", type=int, default=10_000_000)
+    ap.add_argument("--surrogate-ref-photons", type=int, default=100_000_000,
+                    help="photons per held-out reference field")
     ap.add_argument("--surrogate-profile", type=int, default=0, metavar="B",
                     help="profiling case: one surrogate forward+backward at batch B (64^3, c0 32)")
     ap.add_argument("--surrogate-profile-cold", action="store_true",
@@ -758,6 +785,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_other_workloads:
         line["other_workloads"] = other_workloads(spmc, torch, stream, mask70, args.photons)
+        line["profile_mode"] = profile_mode(spmc, torch, stream, mask, args.photons)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mask.copy(), target_s=args.cpu_seconds)
         line["cpu_baseline"].pop("photons", None)

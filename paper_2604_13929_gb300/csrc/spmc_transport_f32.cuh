@@ -13,7 +13,10 @@
 //    phase of its voxel;
 //  * every event -- launch, interaction, roulette, exit and path-cap
 //    tallies -- runs in the compacted event phase, where the warp serves
-//    all parked lanes at once; the stepping loop carries none of that code.
+//    all parked lanes at once; the stepping loop carries none of that code;
+//  * in the depth-profile tally mode a lane sums its deposits of the current
+//    depth bin per phase in registers (exact integers) and adds them to the
+//    block's shared-memory bins only when the photon changes bin or ends.
 //
 // Batched launches (kBatch) run many problems (masks, sizes, optics) in one
 // persistent launch: a warp claims chunks of photons of ONE problem at a
@@ -32,7 +35,9 @@
 
 namespace spmc {
 
-// Resident 256-thread CTAs per SM requested from the register allocator.
+// Resident 256-thread CTAs per SM requested from the register allocator for
+// the voxel-field kernels (the depth-profile kernels ask for 4: without the
+// field REDs they gain from the extra warps, the field kernels did not).
 #ifndef SPMC_F32_MIN_BLOCKS
 #define SPMC_F32_MIN_BLOCKS 3
 #endif
@@ -42,7 +47,7 @@ namespace spmc {
 enum { L_STEP = 0, L_INTERACT = 1, L_FINISH = 2, L_NEW = 3, L_WAIT = 4, L_DONE = 5 };
 
 template <bool kField, bool kMirror, bool kBatch>
-__global__ void __launch_bounds__(256, kBatch ? 3 : SPMC_F32_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, kBatch ? 3 : (kField ? SPMC_F32_MIN_BLOCKS : 4))
 transport_f32_kernel(const TransportParams p, const BatchParams bp) {
     // dynamic shared memory: the staged entry slab of mask bricks, or
     // (batched) one SmemTallies per warp
@@ -141,6 +146,15 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
     float tmx = kInf, tmy = kInf, tmz = 1, dtx = kInf, dty = kInf, dtz = 1, t = 0;
     float fx = 0, fy = 0, fz = 0;
     u32 event = 1, n_int = 0, n_surv = 0, n_steps = 0, n_solid = 0, iters = 0;
+    u64 acc_s = 0, acc_p = 0;           // profile mode: current bin's solid / pore sums
+    auto flush_bin = [&]() {
+        if constexpr (!kField) {
+            if (acc_s) atomicAdd(&st.depth[0][bin], acc_s);
+            if (acc_p) atomicAdd(&st.depth[1][bin], acc_p);
+            acc_s = 0;
+            acc_p = 0;
+        }
+    };
 
     for (;;) {
         // ---- event phase: exits, claims, launches, interactions ------------
@@ -150,6 +164,7 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
         if (__popc(parked) >= compact_k || !stepping) {
             if (mode == L_FINISH) {
                 // kind: 1 R, 2 T, 3 roulette, 4 path cap
+                flush_bin();
                 const int b = (int)(pid & (kNBatch - 1));
                 if (kind <= 2) {
                     const u64 qw = q32_bits(w);
@@ -424,10 +439,14 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
             if constexpr (kField) {
                 if (q) atomicAdd(field + (((u64)brick << 6) | bit), q);
             } else {
-                if (q) atomicAdd(&st.depth[pore ? 1 : 0][bin], q);
+                if (pore) acc_p += q; else acc_s += q;
             }
-            if (gate) { mode = L_FINISH; kind = 4; break; }
-            if (inter) { t += seg; mode = L_INTERACT; break; }
+            if (gate || inter || leaves) {           // the photon leaves the pass
+                if (gate) { mode = L_FINISH; kind = 4; }
+                else if (inter) { t += seg; mode = L_INTERACT; }
+                else { mode = L_FINISH; kind = niz < 0 ? 1 : 2; }
+                break;
+            }
             tau -= need;
 
             // face crossing: commit the next voxel
@@ -439,14 +458,18 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
                 tmx -= t; tmy -= t; tmz -= t;
                 t = 0;
             }
-            if (leaves) { mode = L_FINISH; kind = niz < 0 ? 1 : 2; break; }
             if (rx) { ux = -ux; sx = -sx; } else if (wx) kx += sx;
             if (ry) { uy = -uy; sy = -sy; } else if (wy) ky += sy;
             ix = nix; iy = niy; iz = niz;
             brick = nbrick;
             word = nword;
             bit = bit_of(ix, iy, iz);
-            if constexpr (!kField) if (ax_z) bin = bin_of(iz);
+            if constexpr (!kField) {
+                if (ax_z) {
+                    const int nb = bin_of(iz);
+                    if (nb != bin) { flush_bin(); bin = nb; }
+                }
+            }
         }
     }
 

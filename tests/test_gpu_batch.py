@@ -82,9 +82,10 @@ def test_one_launch_batch_is_independent_of_launch_shape(spmc, problems, steps_p
 
 def test_one_launch_batch_against_oracle(spmc, problems):
     """A batched problem on the same Philox streams as the FP64 oracle: R/T/A
-    within 2e-4 and the integer event counts within 0.5 %.  FP32 histories
-    diverge from FP64 across interfaces (more so with ~100 interactions per
-    photon, as in problem 3), so the aggregate counts agree statistically,
+    within 2e-4 and the integer event counts within 4 sqrt(count) + 0.5 %.
+    FP32 histories diverge from FP64 across interfaces (more so with ~100
+    interactions per photon, as in problem 3), so the aggregate counts agree
+    statistically -- rare ones such as roulette kills to Poisson accuracy --
     not to the last event."""
     from oracle import oracle as orc
     n = [20000, 20000, 20000, 20000]
@@ -97,7 +98,8 @@ def test_one_launch_batch_against_oracle(spmc, problems):
             for k in ("R", "T", "A"):
                 assert abs(t[k] - o[k]) < 2e-4, (i, k, t[k], o[k])
             for k in ("interactions", "exit_R", "exit_T", "rr_kill", "steps", "solid_steps"):
-                assert abs(t[k] - o["counts"][k]) <= max(5, 5e-3 * o["counts"][k]), (i, k, t[k], o["counts"][k])
+                ok = o["counts"][k]
+                assert abs(t[k] - ok) <= 4 * ok ** 0.5 + 5e-3 * ok + 5, (i, k, t[k], ok)
 
 
 @pytest.mark.parametrize("mode", [0, 1])
