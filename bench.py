@@ -735,11 +735,14 @@ def main():
     # 256^3 volume, with and without one Q32.32 RED per step into a 256^3 field
     ceil_red = spmc.sp_mc_probe_step_ceiling(N_VOX, True)["steps_per_s"]
     ceil_nored = spmc.sp_mc_probe_step_ceiling(N_VOX, False)["steps_per_s"]
+    ceil_fit = spmc.sp_mc_probe_step_ceiling(240, True)["steps_per_s"]
     roofline["step_ceiling"] = {
         "with_field_red_steps_per_s": ceil_red, "without_red_steps_per_s": ceil_nored,
+        "with_field_red_240cubed_steps_per_s": ceil_fit,
         "frac_of_red_ceiling": value * steps_per_photon / ceil_red,
         "note": "sp_mc_probe_step_ceiling: the kernel's traversal and tally memory pattern "
-                "with no physics; the 256^3 Q32.32 field (134 MB) exceeds L2"}
+                "with no physics; the 256^3 Q32.32 field (134 MB) is past the L2 knee, a 240^3 "
+                "field (111 MB) is not"}
 
     # end to end through the C ABI with host buffers: upload + pack the host
     # mask, transport, normalise, copy the results back

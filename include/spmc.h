@@ -91,13 +91,8 @@ enum sp_option {
                                 warp vote, branch-free phases, all events in
                                 the compacted event phase); 0 the generic
                                 template kernel (same photons, same method) */
-    SP_OPT_STEPS_PER_PASS = 17, /* streamlined kernel: voxel steps a lane
+    SP_OPT_STEPS_PER_PASS = 17 /* streamlined kernel: voxel steps a lane
                                 takes per pass of its warp, [1, 64] (8);
-                                results do not depend on it                */
-    SP_OPT_L2_PERSIST  = 18  /* 1: persisting-L2 access-policy window over
-                                the voxel field for FP32 field launches
-                                (raises this process's persisting set-aside
-                                to the device maximum); 0 (default): none;
                                 results do not depend on it                */
 };
 
@@ -225,7 +220,7 @@ const char *sp_mc_version(void);
 /*
  * Measurement helper with no counterpart in the paper: the throughput ceiling
  * of the transport kernel's memory pattern on this GPU.  Straight rays step
- * face by face through an all-pore n^3 volume (n a power of two in
+ * face by face through an all-pore n^3 volume (n a multiple of 4 in
  * [16, 1024]) with the transport kernel's traversal arithmetic and mask-brick
  * fetches, and, when red != 0, one Q32.32 RED.ADD.U64 per step into an n^3
  * brick-layout field (8 n^3 bytes, allocated and freed by the call).  One

@@ -75,7 +75,6 @@ struct sp_mc {
     int mirror = 0;         // lateral faces: 0 periodic, 1 mirrors
     int variant = 1;        // FP32 kernel: 0 generic template, 1 streamlined
     int steps_per_pass = 8; // streamlined FP32 kernel: voxel steps per warp pass
-    int l2_persist = 0;     // persisting-L2 window over the field
     u32 bin_mul = 0;        // depth bin by multiply-high, when exact for this nz
     int bin_exact = 0;
     // device memory
@@ -601,9 +600,6 @@ int sp_mc_set_option(sp_mc_t *h, int key, double value) {
     case SP_OPT_STEPS_PER_PASS:
         if (value < 1 || value > 64) return fail(SP_EINVAL, "steps per pass must be in [1, 64]");
         h->steps_per_pass = (int)value; return SP_OK;
-    case SP_OPT_L2_PERSIST:
-        if (value != 0 && value != 1) return fail(SP_EINVAL, "L2 persistence must be 0 or 1");
-        h->l2_persist = (int)value; return SP_OK;
     default: return fail(SP_EINVAL, "unknown option %d", key);
     }
 }
@@ -627,36 +623,8 @@ int sp_mc_get_option(const sp_mc_t *h, int key, double *value) {
     case SP_OPT_LATERAL_BC: *value = h->mirror; return SP_OK;
     case SP_OPT_KERNEL: *value = h->variant; return SP_OK;
     case SP_OPT_STEPS_PER_PASS: *value = h->steps_per_pass; return SP_OK;
-    case SP_OPT_L2_PERSIST: *value = h->l2_persist; return SP_OK;
     default: return fail(SP_EINVAL, "unknown option %d", key);
     }
-}
-
-// Persisting-L2 access-policy window over the voxel field.  The field of the
-// headline volume (256^3 x 8 B = 134 MB) is a little larger than the L2, so
-// plain replacement keeps evicting lines that the next REDs need; a
-// persisting window over the field with hitRatio = set-aside / window keeps a
-// fixed share of its lines resident.  The set-aside is a limit of this
-// process's CUDA context (cudaLimitPersistingL2CacheSize, raised here to the
-// device maximum when it is lower); it ends with the context and changes
-// nothing that outlives the process.
-static int persist_window(sp_mc *h, LaunchExtras *ex) {
-    int max_persist = 0, max_window = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h->device));
-    CUDA_TRY(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, h->device));
-    if (max_persist <= 0 || max_window <= 0) return SP_OK;     // not supported: plain launch
-    size_t cur = 0;
-    CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
-    if (cur < (size_t)max_persist) {
-        CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist));
-        CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
-    }
-    const size_t bytes = std::min<size_t>(h->n_field * sizeof(u64), (size_t)max_window);
-    if (!cur || !bytes) return SP_OK;
-    ex->window = h->d_field;
-    ex->window_bytes = bytes;
-    ex->hit_ratio = (float)std::min(1.0, (double)cur / (double)bytes);
-    return SP_OK;
 }
 
 // One single-problem transport launch of n_photons from photon id pid_begin
@@ -716,10 +684,6 @@ static int launch_run(sp_mc *h, u64 n_photons, u64 seed, u64 pid_begin, const u6
 
     LaunchExtras ex;
     ex.variant = h->variant;
-    if (!f64 && field && h->l2_persist) {
-        const int rc = persist_window(h, &ex);
-        if (rc) return rc;
-    }
     CUDA_TRY(cudaMemsetAsync(&h->d_tal->next, 0, sizeof(u64), s));
     CUDA_TRY(f64 ? launch_transport_f64(p, field, blocks, h->threads, smem, s)
                  : launch_transport_f32(p, field, blocks, h->threads, smem, s, ex));

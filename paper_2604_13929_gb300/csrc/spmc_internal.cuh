@@ -104,13 +104,9 @@ struct BatchParams {
     int steps_per_pass;
 };
 
-// Launch choices of the FP32 path beyond TransportParams: which kernel, and
-// an optional L2 access-policy window (persisting lines) over the field.
+// Launch choices of the FP32 path beyond TransportParams: which kernel.
 struct LaunchExtras {
     int variant = 1;               // 0 generic template kernel, 1 streamlined FP32 kernel
-    void *window = nullptr;        // base of the persisting window (nullptr: none)
-    size_t window_bytes = 0;
-    float hit_ratio = 0.0f;
 };
 
 // Launch helpers (defined in the per-precision translation units).

@@ -20,16 +20,19 @@ __device__ __forceinline__ u64 probe_q32(float c) {    // same rounding as the t
     return ((u64)(u32)k1 << 23) + (u64)(long long)k2;
 }
 
-// Straight rays through an all-pore n^3 volume (n a power of two), periodic in
-// all three axes, mask bricks fetched as in the transport kernel, and (when
+// Straight rays through an all-pore n^3 volume (n a multiple of 4), periodic
+// in all three axes, mask bricks fetched as in the transport kernel, and (when
 // red) one RED.ADD.U64 per step into a brick-layout field.  Rays start at
 // pseudo-random points with pseudo-random directions (a per-thread LCG).
+// Every coordinate stays in [0, n), so brick < (n/4)^3 and the field word
+// index brick * 64 + bit < n^3.
 __global__ void __launch_bounds__(256) probe_kernel(u64 *field, const u64 *bricks, int n,
                                                     long long steps, int red, float *sink) {
     u32 s = 2654435761u * (blockIdx.x * blockDim.x + threadIdx.x + 1);
     auto rnd = [&]() { s = s * 1664525u + 1013904223u; return (float)(s >> 8) * (1.0f / 16777216.0f); };
-    const int nb = n >> 2, m = n - 1;
-    int ix = (int)(rnd() * n) & m, iy = (int)(rnd() * n) & m, iz = (int)(rnd() * n) & m;
+    const int nb = n >> 2;
+    auto wrap = [&](int i) { return i < 0 ? n - 1 : (i >= n ? 0 : i); };
+    int ix = min((int)(rnd() * n), n - 1), iy = min((int)(rnd() * n), n - 1), iz = min((int)(rnd() * n), n - 1);
     float ux = rnd() - 0.5f, uy = rnd() - 0.5f, uz = rnd() - 0.5f;
     const float inv = rsqrtf(ux * ux + uy * uy + uz * uz + 1e-12f);
     ux *= inv; uy *= inv; uz *= inv;
@@ -46,8 +49,8 @@ __global__ void __launch_bounds__(256) probe_kernel(u64 *field, const u64 *brick
         if (tmy < tn) { tn = tmy; ax = 1; }
         if (tmx < tn) { tn = tmx; ax = 0; }
         const float seg = tn - t;
-        const int nix = (ix + (ax == 0 ? sx : 0)) & m, niy = (iy + (ax == 1 ? sy : 0)) & m,
-                  niz = (iz + (ax == 2 ? sz : 0)) & m;
+        const int nix = wrap(ix + (ax == 0 ? sx : 0)), niy = wrap(iy + (ax == 1 ? sy : 0)),
+                  niz = wrap(iz + (ax == 2 ? sz : 0));
         const u32 nbk = ((u32)(niz >> 2) * nb + (niy >> 2)) * nb + (nix >> 2);
         const u64 nword = nbk != brick ? __ldg(bricks + nbk) : word;
         acc += ((word >> bit) & 1ull) ? seg : 0.0f;
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(256) probe_kernel(u64 *field, const u64 *brick
 
 extern "C" int sp_mc_probe_step_ceiling(int n, int red, long long steps_per_thread, double *ms,
                                         double *steps_per_s) {
-    if (n < 16 || n > 1024 || (n & (n - 1)) || steps_per_thread < 1 || !ms || !steps_per_s)
+    if (n < 16 || n > 1024 || (n & 3) || steps_per_thread < 1 || !ms || !steps_per_s)
         return SP_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||

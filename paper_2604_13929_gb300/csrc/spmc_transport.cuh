@@ -35,13 +35,15 @@ namespace cg = cooperative_groups;
 // ------------------------------------------------------------------ RNG --
 
 // Philox4x32-10 (Salmon et al., SC'11): two 32x32 -> 64-bit products per
-// round, key bumped by the Weyl constants between rounds.
+// round (each one wide multiply giving both halves), key bumped by the Weyl
+// constants between rounds.
 __device__ __forceinline__ void philox4x32_10(u32 c0, u32 c1, u32 c2, u32 c3, u32 k0, u32 k1,
                                               u32 out[4]) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const u32 lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const u32 lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const u64 p0 = (u64)0xD2511F53u * c0, p1 = (u64)0xCD9E8D57u * c2;
+        const u32 lo0 = (u32)p0, hi0 = (u32)(p0 >> 32);
+        const u32 lo1 = (u32)p1, hi1 = (u32)(p1 >> 32);
         c0 = hi1 ^ c1 ^ k0;
         c1 = lo1;
         c2 = hi0 ^ c3 ^ k1;
@@ -58,8 +60,11 @@ template <typename Real> struct Ops;
 
 template <> struct Ops<float> {
     __device__ static float inf() { return __int_as_float(0x7f800000); }
-    __device__ static float uniform(u32 r) {               // (2 (r>>9) + 1) 2^-24, exact
-        return __uint2float_rn(((r >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+    // (2 (r>>9) + 1) 2^-24, exact: the float 1 + (r>>9) 2^-23 built from its
+    // bit pattern, minus 1 - 2^-24 (both multiples of 2^-24, the difference
+    // has at most 24 significant bits, so the subtraction is exact)
+    __device__ static float uniform(u32 r) {
+        return __uint_as_float(0x3f800000u | (r >> 9)) - 0.999999940395355225f;
     }
     __device__ static float neg_log(float u) { return -__logf(u); }
     __device__ static void sincos_2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }

@@ -34,38 +34,16 @@ const void *kernel_f32(bool field, bool mirror, int variant) {
 
 cudaError_t launch_transport_f32(const TransportParams &p, bool field, int blocks, int threads,
                                  size_t smem, cudaStream_t s, const LaunchExtras &e) {
-    if (e.variant == 0 && !e.window) return launch_transport<float>(p, field, blocks, threads, smem, s);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    if (e.window && e.window_bytes) {
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = e.window;
-        attr[0].val.accessPolicyWindow.num_bytes = e.window_bytes;
-        attr[0].val.accessPolicyWindow.hitRatio = e.hit_ratio;
-        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-    }
+    if (e.variant == 0) return launch_transport<float>(p, field, blocks, threads, smem, s);
     const BatchParams none{};
-    if (e.variant == 0) {
-        if (p.mirror) {
-            if (field) return cudaLaunchKernelEx(&cfg, transport_kernel<float, true, false, true>, p, none);
-            return cudaLaunchKernelEx(&cfg, transport_kernel<float, false, false, true>, p, none);
-        }
-        if (field) return cudaLaunchKernelEx(&cfg, transport_kernel<float, true, false, false>, p, none);
-        return cudaLaunchKernelEx(&cfg, transport_kernel<float, false, false, false>, p, none);
-    }
     if (p.mirror) {
-        if (field) return cudaLaunchKernelEx(&cfg, transport_f32_kernel<true, true, false>, p, none);
-        return cudaLaunchKernelEx(&cfg, transport_f32_kernel<false, true, false>, p, none);
+        if (field) transport_f32_kernel<true, true, false><<<blocks, threads, smem, s>>>(p, none);
+        else transport_f32_kernel<false, true, false><<<blocks, threads, smem, s>>>(p, none);
+    } else {
+        if (field) transport_f32_kernel<true, false, false><<<blocks, threads, smem, s>>>(p, none);
+        else transport_f32_kernel<false, false, false><<<blocks, threads, smem, s>>>(p, none);
     }
-    if (field) return cudaLaunchKernelEx(&cfg, transport_f32_kernel<true, false, false>, p, none);
-    return cudaLaunchKernelEx(&cfg, transport_f32_kernel<false, false, false>, p, none);
+    return cudaGetLastError();
 }
 
 cudaError_t occupancy_f32(bool field, bool mirror, int variant, int threads, size_t smem,

@@ -29,7 +29,7 @@ NBATCH, NBIN, NHIST = 16, 64, 257
 OPT = {"path_cap": 1, "rr_weight": 2, "rr_mult": 3, "tally_field": 4, "precision": 5,
        "records": 6, "blocks": 7, "threads": 8, "iter_limit": 9, "smem_bricks": 10,
        "pid_offset": 11, "compact": 12, "graph": 13, "lateral_bc": 14, "batch_mode": 15,
-       "kernel": 16, "steps_per_pass": 17, "l2_persist": 18}
+       "kernel": 16, "steps_per_pass": 17}
 ERR_NAMES = {SP_EINVAL: "SP_EINVAL", SP_ENOMEM: "SP_ENOMEM", SP_ECUDA: "SP_ECUDA",
              SP_ESTEPLIMIT: "SP_ESTEPLIMIT", SP_EOVERFLOW: "SP_EOVERFLOW"}
 
@@ -271,7 +271,8 @@ def sp_mc_version() -> str:
 
 
 def sp_mc_probe_step_ceiling(n: int, red: bool, steps_per_thread: int = 20000) -> dict:
-    """Measured stepping ceiling (steps/s) of the transport's memory pattern."""
+    """Measured stepping ceiling (steps/s) of the transport's memory pattern
+    through an n^3 volume (n a multiple of 4)."""
     ms, rate = _D(), _D()
     _check(load().sp_mc_probe_step_ceiling(int(n), 1 if red else 0, int(steps_per_thread),
                                            ctypes.byref(ms), ctypes.byref(rate)))

@@ -313,7 +313,7 @@ def test_bitwise_determinism_across_runs_configs_and_splits(spmc, c1_mask):
     for opt in ({}, {"threads": 128}, {"blocks": 37, "threads": 64}, {"split": True},
                 {"smem_bricks": 2048}, {"compact": 1}, {"compact": 32},
                 {"steps_per_pass": 1}, {"steps_per_pass": 29, "compact": 5},
-                {"l2_persist": 1}):
+                {"kernel": 1, "threads": 96}):
         t, f = run(**opt)
         assert np.array_equal(f, base_f), opt
         for k in ("raw_R", "raw_T", "raw_A", "raw_gated", "raw_lost", "raw_gain", "raw_hist",
