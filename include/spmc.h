@@ -241,10 +241,8 @@ size_t sp_mc_result_size(void);
  * a time).  Each problem has its own bit-packed mask, Q32.32 voxel field and
  * integer tallies, exactly as an sp_mc_create handle.  With the streamlined
  * kernel (SP_OPT_KERNEL = 1, default) every warp claims chunks of 2048
- * photons of one problem from that problem's own counter, starting on a
- * problem picked by its warp index and moving to the next problem only when
- * its problem has no chunk left; it keeps the problem's tallies in shared
- * memory until it moves on; with the generic kernel (0)
+ * photons of one problem from a shared counter and keeps that problem's
+ * tallies in shared memory until it moves on; with the generic kernel (0)
  * photons of all problems are claimed one by one, so lanes of a warp carry
  * different problems.  With the same seed and photon counts every problem's
  * tallies equal those of a separate sp_mc_run on its own handle (same kernel

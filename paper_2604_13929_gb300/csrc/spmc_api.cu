@@ -1028,12 +1028,6 @@ __global__ void batch_advance_kernel(BatchProblem *table, int n) {
     if (i < n) table[i].pid_begin += table[i].n_photons;
 }
 
-// Before a one-launch batched run: every problem's chunk counter to zero.
-__global__ void batch_claim_reset_kernel(BatchProblem *table, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) table[i].tal->next = 0;
-}
-
 struct sp_mc_batch {
     int device = 0, sm_count = 0, n = 0;
     std::vector<sp_mc *> h;
@@ -1043,6 +1037,7 @@ struct sp_mc_batch {
     int threads = 128, blocks_per_sm = 0, compact_k = 8, use_graph = 1, mode = 0;
     int variant = 1, steps_per_pass = 8;   // one-launch kernel and its steps per pass
     u32 chunk = 2048;                      // photons per warp claim (streamlined kernel)
+    u64 total_chunks = 0;
     bool any_mirror = false;
     bool table_valid = false;              // device table matches table[]
     std::vector<u64> cfg_n;                // configuration of the device table / graph
@@ -1218,6 +1213,7 @@ static int batch_launch(sp_mc_batch *b, u64 total, cudaStream_t s) {
     bp.problems = b->d_table;
     bp.n_problems = b->n;
     bp.total_photons = total;
+    bp.total_chunks = b->total_chunks;
     bp.chunk = b->chunk;
     bp.next = b->d_next;
     bp.key0 = (u32)b->cfg_seed;
@@ -1225,10 +1221,6 @@ static int batch_launch(sp_mc_batch *b, u64 total, cudaStream_t s) {
     bp.compact_k = b->compact_k;
     bp.steps_per_pass = b->steps_per_pass;
     CUDA_TRY(cudaMemsetAsync(b->d_next, 0, sizeof(u64), s));
-    if (b->variant != 0) {
-        batch_claim_reset_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_table, b->n);
-        CUDA_TRY(cudaGetLastError());
-    }
     CUDA_TRY(launch_transport_batch(bp, b->variant, b->any_mirror, per_sm * b->sm_count, b->threads, s));
     batch_advance_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_table, b->n);
     CUDA_TRY(cudaGetLastError());
@@ -1264,7 +1256,7 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
     const bool same_cfg = b->table_valid && want == b->cfg_n && seed == b->cfg_seed;
     if (!same_cfg) {
         // (re)build the device table from the handles' photon counters
-        u64 offset = 0;
+        u64 offset = 0, chunk_begin = 0;
         for (int i = 0; i < b->n; ++i) {
             sp_mc *h = b->h[i];
             BatchProblem &t = b->table[i];
@@ -1278,6 +1270,8 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
             t.n_photons = n_photons[i];
             t.offset = offset;
             offset += n_photons[i];
+            t.chunk_begin = chunk_begin;
+            chunk_begin += (n_photons[i] + b->chunk - 1) / b->chunk;
             const u64 lim = iter_limit(h);
             t.iter_limit = lim > 0xffffffffull ? 0xffffffffu : (u32)lim;
             fill_f32(h, path_cap(h), t.f32, t.hg_iso, t.small_x);
@@ -1287,6 +1281,7 @@ extern "C" int sp_mc_batch_run(sp_mc_batch_t *b, const uint64_t *n_photons, uint
         CUDA_TRY(cudaMemcpyAsync(b->d_table, b->table.data(), b->n * sizeof(BatchProblem),
                                  cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaStreamSynchronize(s));     // the host table may change after return
+        b->total_chunks = chunk_begin;
         b->cfg_n = want;
         b->cfg_seed = seed;
         b->table_valid = true;

@@ -78,15 +78,15 @@ struct TransportParams {
 // claim counter: global index k belongs to the problem whose
 // [offset, offset + n_photons) contains it, with photon id pid_begin + k - offset.
 // The streamlined FP32 kernel claims work in chunks of `chunk` photons of one
-// problem per warp, from the problem's own counter (its tallies' `next`,
-// zeroed before each launch): chunk c holds the problem's photon indices
-// [c chunk, min((c + 1) chunk, n_photons)).
+// problem per warp: problem i owns the global chunk indices
+// [chunk_begin, chunk_begin + ceil(n_photons / chunk)).
 struct BatchProblem {
     const u64 *bricks;
     u64 *field;
     DevTallies *tal;
     int nx, ny, nz, nbx, nby, nbz;
     u64 pid_begin, n_photons, offset;
+    u64 chunk_begin;
     u32 iter_limit;
     int hg_iso, small_x, mirror;
     TransportParams::F32 f32;
@@ -96,6 +96,7 @@ struct BatchParams {
     const BatchProblem *problems;   // device table
     int n_problems;
     u64 total_photons;              // sum of n_photons (one run)
+    u64 total_chunks;               // chunks over all problems (streamlined kernel)
     u32 chunk;                      // photons per chunk (streamlined kernel)
     u64 *next;                      // claim counter, zeroed before each launch
     u32 key0, key1;                 // Philox key = seed (shared by all problems)

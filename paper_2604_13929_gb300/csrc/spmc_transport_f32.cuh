@@ -20,12 +20,10 @@
 //
 // Batched launches (kBatch) run many problems (masks, sizes, optics) in one
 // persistent launch: a warp claims chunks of photons of ONE problem at a
-// time from that problem's own chunk counter, so the problem's constants are
-// uniform across the warp and its block tallies stay in shared memory (one
-// set per warp, flushed to the problem's global tallies when the warp moves
-// on to another problem).  Warps start spread over the problems and move on
-// only when their problem has no chunk left, and only once every photon they
-// carry has finished.
+// time, so the problem's constants are uniform across the warp and its block
+// tallies stay in shared memory (one set per warp, flushed to the problem's
+// global tallies when the warp moves on to another problem).  A warp changes
+// problem only once every photon it carries has finished.
 //
 // Per photon the arithmetic depends only on its id, its problem and the mask,
 // never on the warp it runs in, so the integer tallies are bit-identical
@@ -88,8 +86,7 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
     bool mirror = kMirror && p.mirror != 0;
     int prob = -1;                      // batched: the warp's current problem
     u64 ck_next = 0, ck_end = 0;        // batched: photon indices left in its chunk
-    long long pend = -1;                // batched: a claimed chunk not yet started,
-    int pend_prob = -1;                 //   and its problem
+    long long pend = -1;                // batched: a claimed chunk not yet started
     const u64 pid0 = kBatch ? 0 : (p.pid_begin_dev ? *p.pid_begin_dev : p.pid_begin);
 
     auto brick_of = [&](int ix, int iy, int iz) -> u32 {
@@ -239,34 +236,21 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
                         continue;
                     }
                     if (pend < 0) {
-                        // the next chunk of this warp's problem; once it has
-                        // none left, of the following problems in turn.  A warp
-                        // starts on problem (its global index mod n), so warps
-                        // spread over the problems and each changes problem
-                        // only a few times.
-                        const int start = prob >= 0 ? prob
-                                                    : (int)(((u64)blockIdx.x * (blockDim.x >> 5) + (u64)warp) %
-                                                            (u64)bp.n_problems);
-                        for (int i = 0; i < bp.n_problems; ++i) {
-                            const int q = start + i < bp.n_problems ? start + i : start + i - bp.n_problems;
-                            const BatchProblem &pq = bp.problems[q];
-                            const u64 n_chunks = (pq.n_photons + bp.chunk - 1) / bp.chunk;
-                            if (n_chunks == 0) continue;
-                            u64 c = 0;
-                            if (lane == 0) c = atomicAdd(&pq.tal->next, 1ull);
-                            c = __shfl_sync(kFull, c, 0);
-                            if (c < n_chunks) {
-                                pend = (long long)c;
-                                pend_prob = q;
-                                break;
-                            }
-                        }
+                        u64 c = 0;
+                        if (lane == 0) c = atomicAdd(bp.next, 1ull);
+                        pend = (long long)__shfl_sync(kFull, c, 0);
                     }
-                    if (pend < 0) {                  // every problem is exhausted
+                    if ((u64)pend >= bp.total_chunks) {
                         if (mode == L_NEW) mode = L_DONE;
                         break;
                     }
-                    if (pend_prob != prob) {
+                    // the problem owning chunk pend (last chunk_begin <= pend)
+                    int lo = 0, hi = bp.n_problems - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (bp.problems[mid].chunk_begin <= (u64)pend) lo = mid; else hi = mid - 1;
+                    }
+                    if (lo != prob) {
                         const unsigned busy = __ballot_sync(kFull, mode == L_STEP || mode == L_INTERACT ||
                                                                        mode == L_FINISH);
                         if (busy) {
@@ -274,7 +258,7 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
                             break;
                         }
                         if (prob >= 0) flush_warp(prob);
-                        prob = pend_prob;
+                        prob = lo;
                         const BatchProblem &pr = bp.problems[prob];
                         nx = pr.nx; ny = pr.ny; nz = pr.nz; nbx = pr.nbx; nby = pr.nby;
                         bricks = pr.bricks; field = pr.field; tal = pr.tal;
@@ -284,7 +268,7 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
                         mirror = kMirror && pr.mirror != 0;
                     }
                     const BatchProblem &pr = bp.problems[prob];
-                    ck_next = (u64)pend * (u64)bp.chunk;
+                    ck_next = ((u64)pend - pr.chunk_begin) * (u64)bp.chunk;
                     ck_end = ck_next + (u64)bp.chunk < pr.n_photons ? ck_next + (u64)bp.chunk : pr.n_photons;
                     pend = -1;
                 }
