@@ -69,6 +69,11 @@ int spnn_status(void* stream);
  *   SPNN_OPT_CONV_FULL_HALO 1: conv3 forward / input gradient on 8 x 16 tiles whose
  *                           one box per plane block serves all 27 taps, where it
  *                           fits; 0 (default): one box per x-shift
+ *   SPNN_OPT_ROWS_PERSISTENT k >= 1: forward / input-gradient GEMMs launch k
+ *                           CTAs per resident slot that the occupancy query
+ *                           reports (default 2: the query has answered one CTA
+ *                           per SM where two are resident), each claiming tiles
+ *                           in order until none are left; 0: one CTA per tile
  * Settings that do not fit a layer fall back to the automatic choice.
  */
 #define SPNN_OPT_CONV_SUBTILES 1
@@ -76,6 +81,7 @@ int spnn_status(void* stream);
 #define SPNN_OPT_STAGE_KB 3
 #define SPNN_OPT_WGRAD_HALO 4
 #define SPNN_OPT_CONV_FULL_HALO 5
+#define SPNN_OPT_ROWS_PERSISTENT 7
 int spnn_set_option(int key, int value);
 
 /* Elements (BF16) of a packed weight operand for a layer. */

@@ -20,6 +20,11 @@ namespace {
 
 thread_local std::string g_error;
 __device__ int g_err_flag;
+// Tile claim counters of the persistent rows GEMM: each launch takes the next
+// of kCtrSlots rows and zeroes it on its stream first, so up to kCtrSlots
+// launches may be in flight on different streams at once.
+constexpr int kCtrSlots = 64;
+__device__ int g_tile_ctr[kCtrSlots][spnn::kMaxGridN];
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -162,7 +167,8 @@ void rows_geometry(RowsParams& p) {
 
 // Launch tuning (spnn_set_option): conv3 subtiles per CTA, chunk planes per
 // K-step, and the shared-memory budget of the stage ring; 0 = automatic.
-int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0, g_opt_wgrad_halo = 1, g_opt_full_halo = 0;
+int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0, g_opt_wgrad_halo = 1, g_opt_full_halo = 0,
+    g_opt_rows_persistent = 2;
 
 int stage_budget() { return (g_opt_stage_kb > 0 ? g_opt_stage_kb : 110) * 1024; }
 
@@ -245,18 +251,35 @@ int rows_gemm(RowsParams& p, cudaStream_t st) {
     if (p.n_total > 256 && p.n_total % 256) return fail(SPNN_EINVAL, "GEMM N %d > 256 not a multiple of 256", p.n_total);
     if (p.kc_total < 2 || p.kc_total % 2) return fail(SPNN_EINVAL, "input channels not a multiple of 16");
     rows_geometry(p);
-    int S = (int)((uint32_t)stage_budget() / p.stage_bytes);
-    p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
     if (p.mt < 1) p.mt = 1;
+    // two accumulator buffers where they fit in TMEM; a CTA whose buffers take
+    // all 512 columns runs alone on its SM, so its ring may use twice the budget
+    p.nbuf = 2 * p.mt * p.n_tile <= 512 ? 2 : 1;
+    const bool alone = tmem_cols(p.nbuf * p.mt * p.n_tile) > 256;
+    const uint32_t budget = (uint32_t)stage_budget() * (alone && g_opt_stage_kb <= 0 ? 2u : 1u);
+    int S = (int)(budget / p.stage_bytes);
+    p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
+    p.tiles = (int)n_tiles(p.g);
+    p.persistent = g_opt_rows_persistent;
     // K-major no-swizzle operands: leading-dimension offset = step between
     // 16-byte chunk planes along K, stride-dimension offset = step between
     // 8-row groups (128 bytes); the kernel builds the descriptors.
     p.idesc = idesc_bf16(128, p.n_tile, 0, 0);
     p.err = err_ptr();
     if (!p.err) return fail(SPNN_ECUDA, "no device");
-    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
+    const int grid_n = p.n_total / p.n_tile;
+    if (grid_n > kMaxGridN) return fail(SPNN_EINVAL, "GEMM N %d: more than %d N tiles", p.n_total, kMaxGridN);
+    static unsigned ctr_next = 0;
+    void* ctr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ctr, g_tile_ctr);
+    if (e != cudaSuccess) return cuda_fail(e, "tile counters");
+    p.tile_ctr = static_cast<int*>(ctr) + (size_t)(ctr_next++ % kCtrSlots) * kMaxGridN;
+    e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int) * grid_n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tile counter reset");
+    // stages, alignment slack, 2 S + 12 mbarriers, four tile slots and the TMEM address slot
+    size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 15) * 8;
     if (smem > 227 * 1024) return fail(SPNN_EINVAL, "stage of %u bytes does not fit", p.stage_bytes);
-    cudaError_t e = launch_rows(p, (int)n_tiles(p.g), p.n_total / p.n_tile, smem, st);
+    e = launch_rows(p, grid_n, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "rows_kernel launch");
     return SPNN_OK;
 }
@@ -909,6 +932,9 @@ int spnn_set_option(int key, int value) {
         return SPNN_OK;
     case SPNN_OPT_CONV_FULL_HALO:
         g_opt_full_halo = value != 0;
+        return SPNN_OK;
+    case SPNN_OPT_ROWS_PERSISTENT:
+        g_opt_rows_persistent = value < 0 ? 0 : value;
         return SPNN_OK;
     default:
         return fail(SPNN_EINVAL, "unknown option %d", key);

@@ -115,25 +115,62 @@ __device__ __forceinline__ void issue_conv_step(int mt, int eh, uint32_t tmem, u
 // Rows GEMM (forward, input-gradient and transposed-conv layers).
 // A tile: kc_step chunk planes of 128 rows x 16 bytes (2 KB each), K-major;
 // B tile: kc_step planes of n_tile rows x 16 bytes, K-major.
+//
+// Persistent, dynamically scheduled: the producer claims the next tile from a
+// global counter (so the tiles in flight stay a compact window of the grid,
+// and the halo rows that neighbouring tiles share stay in L2) and hands its
+// index to the MMA and epilogue warps through a ring of four shared slots
+// (tile_full / tile_empty; index -1 ends the CTA).  The stage ring runs on
+// across tiles, so the next tile's operands load while the current one
+// multiplies.  The accumulators of consecutive tiles alternate
+// between two TMEM buffers (nbuf = 2 when they fit in 512 columns): the
+// epilogue of tile i reads one buffer while the MMAs of tile i + 1 fill the
+// other.  acc_full[b] completes when the MMAs of a tile retire
+// (tcgen05.commit), acc_empty[b] when the four epilogue warps have read it.
 // ------------------------------------------------------------------------
+
+// Origin of tile t (32-bit: a lone thread divides once per tile).
+__device__ __forceinline__ void tile_origin_u32(const TileGrid& g, uint32_t t, int& x0, int& y0, int& z0,
+                                                int& b0) {
+    uint32_t q = t / (uint32_t)g.nx;
+    x0 = (int)(t - q * (uint32_t)g.nx) * g.bx;
+    t = q;
+    q = t / (uint32_t)g.ny;
+    y0 = (int)(t - q * (uint32_t)g.ny) * g.by;
+    t = q;
+    q = t / (uint32_t)g.nz;
+    z0 = (int)(t - q * (uint32_t)g.nz) * g.bz;
+    b0 = (int)q * g.bb;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant__ RowsParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align1024(smem_raw);
     const int S = p.stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+    volatile int* tile_slot = reinterpret_cast<volatile int*>(bars + 2 * S + 12);   // [4]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 14);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = smem_u32(bars);
-    const uint32_t done = bar0 + 16u * S;
+    const uint32_t acc_full = bar0 + 16u * S, acc_empty = acc_full + 16u;   // [2] each
+    const uint32_t tile_full = acc_empty + 16u, tile_empty = tile_full + 32u;   // [4] each
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = tmem_cols(p.mt * p.n_tile);   // one accumulator per subtile
+    const uint32_t acc_cols = (uint32_t)(p.mt * p.n_tile);   // one accumulator per subtile
+    const uint32_t ncols = tmem_cols(p.nbuf * (int)acc_cols);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(bar0 + 8u * s, 1);
             mbar_init(bar0 + 8u * (S + s), 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full + 8u * b, 1);
+            mbar_init(acc_empty + 8u * b, 4);
+        }
+        for (int b = 0; b < 4; ++b) {
+            mbar_init(tile_full + 8u * b, 1);
+            mbar_init(tile_empty + 8u * b, 5);   // the MMA warp and the four epilogue warps
+        }
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -144,9 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    int x0, y0, z0, b0;
-    tile_origin(p.g, blockIdx.x, x0, y0, z0, b0);
+    int* const tile_ctr = p.tile_ctr + blockIdx.y;
 
     const bool conv = p.tap_mode == TAP_SHIFT3;
     if (warp == 0) {
@@ -154,56 +189,75 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
             const int gpt = conv ? p.kc_total / p.E : p.kc_total / p.kc_step;
             const uint32_t tx = p.a_stage_bytes + p.b_stage_bytes;
             Ring q;
-            int tap = 0, g = 0;   // K-step k = tap * gpt + g
-            for (int k = 0; k < p.ksteps; ++k, q.next(S), g = (g + 1 < gpt) ? g + 1 : 0, tap += (g == 0)) {
-                const int s = q.s;
-                const uint32_t r = q.r;
-                const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
-                if (k >= S && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
+            bool ok = true;
+            int claimed = atomicAdd(tile_ctr, 1);
+            for (uint32_t it = 0; ok; ++it) {
+                // publish the claimed tile's index (-1: none left) in slot it % 4
+                const uint32_t ts = it & 3u, tu = it >> 2;
+                if (tu > 0 && !mbar_wait(tile_empty + 8u * ts, (tu - 1) & 1u, kWaitLimitNs)) {
                     atomicOr(p.err, ERR_TIMEOUT);
                     break;
                 }
-                mbar_expect_tx(full, tx);
-                const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
-                if (conv && p.halo == 2) {
-                    // full halo: one box of (bx + 2, by + 2, 3) voxels per block of E planes
-                    // holds all 27 taps; the weights of the three x-shifts follow
-                    const int kc = k * p.E;
-                    const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
-                    tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, c8);
-                    const uint32_t bsz = 9u * p.E * p.n_tile * 16u;
-                    for (int dxi = 0; dxi < 3; ++dxi) {
+                const int t = claimed < p.tiles ? claimed : -1;
+                tile_slot[ts] = t;
+                mbar_arrive(tile_full + 8u * ts);
+                if (t < 0) break;
+                // claim the following tile now: the atomic's latency hides behind this tile's loads
+                claimed = atomicAdd(tile_ctr, 1);
+                int x0, y0, z0, b0;
+                tile_origin_u32(p.g, (uint32_t)t, x0, y0, z0, b0);
+                int tap = 0, g = 0;   // K-step k = tap * gpt + g
+                for (int k = 0; k < p.ksteps; ++k, q.next(S), g = (g + 1 < gpt) ? g + 1 : 0, tap += (g == 0)) {
+                    const int s = q.s;
+                    const uint32_t r = q.r;
+                    const uint32_t full = bar0 + 8u * s, empty = bar0 + 8u * (S + s);
+                    if (r > 0 && !mbar_wait(empty, (r - 1) & 1u, kWaitLimitNs)) {
+                        atomicOr(p.err, ERR_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(full, tx);
+                    const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes;
+                    if (conv && p.halo == 2) {
+                        // full halo: one box of (bx + 2, by + 2, 3) voxels per block of E planes
+                        // holds all 27 taps; the weights of the three x-shifts follow
+                        const int kc = k * p.E;
+                        const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
+                        tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, c8);
+                        const uint32_t bsz = 9u * p.E * p.n_tile * 16u;
+                        for (int dxi = 0; dxi < 3; ++dxi) {
+                            const __nv_bfloat16* src =
+                                p.wpack + ((size_t)(blockIdx.y * 3 + dxi) * p.kc_total + kc) * 9 * p.n_tile * 8;
+                            bulk_load(a_dst + p.a_stage_bytes + bsz * dxi, src, bsz, full);
+                        }
+                    } else if (conv) {
+                        // tap = x-shift index, g = block of E chunk planes
+                        const int dx = tap - 1, kc = g * p.E;
+                        const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
+                        if (p.halo) {
+                            tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 + dx), y0 - 1, z0 - 1, b0, c8);
+                        } else {
+                            for (int t9 = 0; t9 < 9; ++t9)
+                                tma_load_5d(a_dst + (uint32_t)(t9 * p.E) * 2048u, &p.maps[mi], full, 8 * (x0 + dx),
+                                            y0 + (t9 % 3) - 1, z0 + (t9 / 3) - 1, b0, c8);
+                        }
                         const __nv_bfloat16* src =
-                            p.wpack + ((size_t)(blockIdx.y * 3 + dxi) * p.kc_total + kc) * 9 * p.n_tile * 8;
-                        bulk_load(a_dst + p.a_stage_bytes + bsz * dxi, src, bsz, full);
-                    }
-                } else if (conv) {
-                    // tap = x-shift index, g = block of E chunk planes
-                    const int dx = tap - 1, kc = g * p.E;
-                    const int mi = kc < p.kc0 ? 0 : 1, c8 = kc < p.kc0 ? kc : kc - p.kc0;
-                    if (p.halo) {
-                        tma_load_5d(a_dst, &p.maps[mi], full, 8 * (x0 + dx), y0 - 1, z0 - 1, b0, c8);
+                            p.wpack + ((size_t)(blockIdx.y * 3 + tap) * p.kc_total + kc) * 9 * p.n_tile * 8;
+                        bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
                     } else {
-                        for (int t9 = 0; t9 < 9; ++t9)
-                            tma_load_5d(a_dst + (uint32_t)(t9 * p.E) * 2048u, &p.maps[mi], full, 8 * (x0 + dx),
-                                        y0 + (t9 % 3) - 1, z0 + (t9 / 3) - 1, b0, c8);
+                        if (p.tap_mode == TAP_MAP) {
+                            for (int j = 0; j < p.kc_step; ++j)
+                                load_box(a_dst + 2048u * j, &p.maps[tap], full, true, g * p.kc_step + j, x0, y0, z0,
+                                         b0, p.g.B);
+                        } else {
+                            // TAP_NONE: one box of kc_step chunk planes
+                            tma_load_5d(a_dst, &p.maps[0], full, 8 * x0, y0, z0, b0, g * p.kc_step);
+                        }
+                        const __nv_bfloat16* src =
+                            p.wpack + ((size_t)(blockIdx.y * p.n_taps + tap) * p.kc_total + (size_t)g * p.kc_step) *
+                                          p.n_tile * 8;
+                        bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
                     }
-                    const __nv_bfloat16* src =
-                        p.wpack + ((size_t)(blockIdx.y * 3 + tap) * p.kc_total + kc) * 9 * p.n_tile * 8;
-                    bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
-                } else {
-                    if (p.tap_mode == TAP_MAP) {
-                        for (int j = 0; j < p.kc_step; ++j)
-                            load_box(a_dst + 2048u * j, &p.maps[tap], full, true, g * p.kc_step + j, x0, y0, z0,
-                                     b0, p.g.B);
-                    } else {
-                        // TAP_NONE: one box of kc_step chunk planes
-                        tma_load_5d(a_dst, &p.maps[0], full, 8 * x0, y0, z0, b0, g * p.kc_step);
-                    }
-                    const __nv_bfloat16* src =
-                        p.wpack + ((size_t)(blockIdx.y * p.n_taps + tap) * p.kc_total + (size_t)g * p.kc_step) *
-                                      p.n_tile * 8;
-                    bulk_load(a_dst + p.a_stage_bytes, src, p.b_stage_bytes, full);
                 }
             }
         }
@@ -221,130 +275,171 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
             tap_off[t9] = p.halo == 1 ? (uint32_t)(((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * p.g.bx)
                                       : (uint32_t)(t9 * p.E) * 128u;
         Ring q;
-        for (int k = 0; k < p.ksteps; ++k, q.next(S)) {
-            const int s = q.s;
-            const uint32_t r = q.r;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
+        bool ok = true;
+        for (uint32_t it = 0; ok; ++it) {
+            const uint32_t ts = it & 3u, tu = it >> 2;
+            if (!__all_sync(0xffffffffu, mbar_wait(tile_full + 8u * ts, tu & 1u, kWaitLimitNs))) {
+                if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            const int t = tile_slot[ts];
+            __syncwarp();
+            if (leader) mbar_arrive(tile_empty + 8u * ts);
+            if (t < 0) break;
+            // accumulator buffer of this tile and how often it was filled before
+            const uint32_t buf = p.nbuf == 2 ? (it & 1u) : 0u, use = p.nbuf == 2 ? (it >> 1) : it;
+            if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(acc_empty + 8u * buf, (use - 1) & 1u, kWaitLimitNs))) {
                 if (leader) atomicOr(p.err, ERR_TIMEOUT);
                 break;
             }
             tc_fence_after();
-            const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
-            const uint32_t b0s = a0 + p.a_stage_bytes;
-            if (conv && p.halo == 2) {
-                if (leader) {
-                    // rows of a subtile are y-runs of bx = 8 voxels: one core-matrix group
-                    // each, (bx + 2) * 16 bytes apart in the halo box; every tap is a
-                    // start offset ((dz, dy) rows, dx * 16 bytes)
-                    const uint32_t rowb = (uint32_t)(p.g.bx + 2) * 16u;
-                    const uint32_t sub = (uint32_t)(kRows / p.g.bx) * rowb;
-                    const uint32_t bsz = 9u * p.E * nrow;
-                    for (int dxi = 0; dxi < 3; ++dxi)
-                        for (int t9 = 0; t9 < 9; ++t9) {
-                            const uint32_t a_tap =
-                                a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb + 16u * dxi;
-                            for (int i = 0; i < p.E / 2; ++i) {
-                                const uint64_t bd =
-                                    smem_desc(b0s + bsz * dxi + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
-                                for (int m = 0; m < p.mt; ++m) {
-                                    const uint64_t ad =
-                                        smem_desc(a_tap + sub * m + 2u * i * p.halo_plane, p.halo_plane, rowb);
-                                    umma_bf16(tmem + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
-                                              (k > 0 || dxi > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+            const uint32_t acc = tmem + buf * acc_cols;
+            for (int k = 0; k < p.ksteps; ++k, q.next(S)) {
+                const int s = q.s;
+                const uint32_t r = q.r;
+                if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8u * s, r & 1u, kWaitLimitNs))) {
+                    if (leader) atomicOr(p.err, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes;
+                const uint32_t b0s = a0 + p.a_stage_bytes;
+                if (conv && p.halo == 2) {
+                    if (leader) {
+                        // rows of a subtile are y-runs of bx = 8 voxels: one core-matrix group
+                        // each, (bx + 2) * 16 bytes apart in the halo box; every tap is a
+                        // start offset ((dz, dy) rows, dx * 16 bytes)
+                        const uint32_t rowb = (uint32_t)(p.g.bx + 2) * 16u;
+                        const uint32_t sub = (uint32_t)(kRows / p.g.bx) * rowb;
+                        const uint32_t bsz = 9u * p.E * nrow;
+                        for (int dxi = 0; dxi < 3; ++dxi)
+                            for (int t9 = 0; t9 < 9; ++t9) {
+                                const uint32_t a_tap =
+                                    a0 + (uint32_t)((t9 / 3) * (p.g.by + 2) + (t9 % 3)) * rowb + 16u * dxi;
+                                for (int i = 0; i < p.E / 2; ++i) {
+                                    const uint64_t bd =
+                                        smem_desc(b0s + bsz * dxi + (uint32_t)(2 * i * 9 + t9) * nrow, 9u * nrow, 128);
+                                    for (int m = 0; m < p.mt; ++m) {
+                                        const uint64_t ad =
+                                            smem_desc(a_tap + sub * m + 2u * i * p.halo_plane, p.halo_plane, rowb);
+                                        umma_bf16(acc + (uint32_t)(m * p.n_tile), ad, bd, p.idesc,
+                                                  (k > 0 || dxi > 0 || t9 > 0 || i > 0) ? 1u : 0u);
+                                    }
                                 }
                             }
-                        }
+                    }
+                } else if (conv) {
+                    const uint64_t ad = smem_desc(a0, a_lbo, 128), bd = smem_desc(b0s, 9u * nrow, 128);
+                    if (leader)
+                        issue_conv_step(p.mt, p.E / 2, acc, ad, bd, tap_off, a_lbo / 8u, (uint32_t)p.n_tile, p.idesc,
+                                        k == 0);
+                } else if (leader) {
+                    for (int i = 0; i < p.kc_step / 2; ++i) {
+                        const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
+                        const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
+                        umma_bf16(acc, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
+                    }
                 }
-            } else if (conv) {
-                const uint64_t ad = smem_desc(a0, a_lbo, 128), bd = smem_desc(b0s, 9u * nrow, 128);
-                if (leader)
-                    issue_conv_step(p.mt, p.E / 2, tmem, ad, bd, tap_off, a_lbo / 8u, (uint32_t)p.n_tile, p.idesc,
-                                    k == 0);
-            } else if (leader) {
-                for (int i = 0; i < p.kc_step / 2; ++i) {
-                    const uint64_t ad = smem_desc(a0 + 4096u * i, 2048u, 128);
-                    const uint64_t bd = smem_desc(b0s + 2u * i * nrow, nrow, 128);
-                    umma_bf16(tmem, ad, bd, p.idesc, (k > 0 || i > 0) ? 1u : 0u);
-                }
+                if (leader) umma_commit(bar0 + 8u * (S + s));
+                __syncwarp();
             }
-            if (leader) umma_commit(bar0 + 8u * (S + s));
+            if (!ok) break;
+            if (leader) umma_commit(acc_full + 8u * buf);
             __syncwarp();
         }
-        if (leader) umma_commit(done);
-        __syncwarp();
     } else {
         const int q = warp & 3;
         const int r = q * 32 + lane;
-        bool ok = mbar_wait(done, 0, kWaitLimitNs);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) {
-            if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
-        } else {
-            tc_fence_after();
-            for (int m = 0; m < p.mt; ++m) {
-                int vx, vy, vz, vb;
-                const long long vox = row_voxel(p.g, x0, y0, z0, b0, m * kRows + r, &vx, &vy, &vz, &vb);
-                float head_acc = 0.f;
-                for (int j = 0; j < p.n_tile / 16; ++j) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * p.n_tile + j * 16), v);
-                    tmem_wait_ld();
-                    const int n0 = blockIdx.y * p.n_tile + j * 16;
-                    const EpiDest& d = (n0 < p.split) ? p.d[0] : p.d[1];
-                    if (d.out == nullptr) continue;
-                    int ch0;
-                    long long off;
-                    if (p.scatter_up) {
-                        const int o = n0 / p.cout_up;
-                        ch0 = n0 % p.cout_up;
-                        const int oz = o >> 2, oy = (o >> 1) & 1, ox = o & 1;
-                        const long long fine = (((long long)vb * (2 * p.g.D) + 2 * vz + oz) * (2 * p.g.H) + 2 * vy + oy) *
-                                                   (2LL * p.g.W) +
-                                               2 * vx + ox;
-                        off = (ch0 >> 3) * d.plane + fine * 8;
-                    } else {
-                        ch0 = n0 - d.col0;
-                        off = (ch0 >> 3) * d.plane + vox * 8;
-                    }
-                    float f[16];
-                    #pragma unroll
-                    for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
-                    if (d.bias) {
+        for (uint32_t it = 0;; ++it) {
+            const uint32_t ts = it & 3u, tu = it >> 2;
+            if (!__all_sync(0xffffffffu, mbar_wait(tile_full + 8u * ts, tu & 1u, kWaitLimitNs))) {
+                if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            const int t = tile_slot[ts];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tile_empty + 8u * ts);
+            if (t < 0) break;
+            const uint32_t buf = p.nbuf == 2 ? (it & 1u) : 0u, use = p.nbuf == 2 ? (it >> 1) : it;
+            if (!__all_sync(0xffffffffu, mbar_wait(acc_full + 8u * buf, use & 1u, kWaitLimitNs))) {
+                if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+                break;
+            }
+            {
+                tc_fence_after();
+                const uint32_t acc = tmem + buf * acc_cols;
+                int x0, y0, z0, b0;
+                tile_origin_u32(p.g, (uint32_t)t, x0, y0, z0, b0);
+                for (int m = 0; m < p.mt; ++m) {
+                    int vx, vy, vz, vb;
+                    const long long vox = row_voxel(p.g, x0, y0, z0, b0, m * kRows + r, &vx, &vy, &vz, &vb);
+                    float head_acc = 0.f;
+                    for (int j = 0; j < p.n_tile / 16; ++j) {
+                        uint32_t v[16];
+                        tmem_ld16(acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * p.n_tile + j * 16), v);
+                        tmem_wait_ld();
+                        const int n0 = blockIdx.y * p.n_tile + j * 16;
+                        const EpiDest& d = (n0 < p.split) ? p.d[0] : p.d[1];
+                        if (d.out == nullptr) continue;
+                        int ch0;
+                        long long off;
+                        if (p.scatter_up) {
+                            const int o = n0 / p.cout_up;
+                            ch0 = n0 % p.cout_up;
+                            const int oz = o >> 2, oy = (o >> 1) & 1, ox = o & 1;
+                            const long long fine = (((long long)vb * (2 * p.g.D) + 2 * vz + oz) * (2 * p.g.H) + 2 * vy + oy) *
+                                                       (2LL * p.g.W) +
+                                                   2 * vx + ox;
+                            off = (ch0 >> 3) * d.plane + fine * 8;
+                        } else {
+                            ch0 = n0 - d.col0;
+                            off = (ch0 >> 3) * d.plane + vox * 8;
+                        }
+                        float f[16];
                         #pragma unroll
-                        for (int i = 0; i < 16; ++i) f[i] += d.bias[ch0 + i];
-                    }
-                    if (d.addend) {
-                        float a[16];
-                        load16_planes(d.addend + off, d.plane, a);
+                        for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+                        if (d.bias) {
+                            #pragma unroll
+                            for (int i = 0; i < 16; ++i) f[i] += d.bias[ch0 + i];
+                        }
+                        if (d.addend) {
+                            float a[16];
+                            load16_planes(d.addend + off, d.plane, a);
+                            #pragma unroll
+                            for (int i = 0; i < 16; ++i) f[i] += a[i];
+                        }
+                        if (d.relu) {
+                            #pragma unroll
+                            for (int i = 0; i < 16; ++i) f[i] = fmaxf(f[i], 0.f);
+                        }
+                        if (d.mask) {
+                            float m[16];
+                            load16_planes(d.mask + off, d.plane, m);
+                            #pragma unroll
+                            for (int i = 0; i < 16; ++i) f[i] = (m[i] > 0.f) ? f[i] : 0.f;
+                        }
+                        uint4 w[2];
+                        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
                         #pragma unroll
-                        for (int i = 0; i < 16; ++i) f[i] += a[i];
-                    }
-                    if (d.relu) {
-                        #pragma unroll
-                        for (int i = 0; i < 16; ++i) f[i] = fmaxf(f[i], 0.f);
-                    }
-                    if (d.mask) {
-                        float m[16];
-                        load16_planes(d.mask + off, d.plane, m);
-                        #pragma unroll
-                        for (int i = 0; i < 16; ++i) f[i] = (m[i] > 0.f) ? f[i] : 0.f;
-                    }
-                    uint4 w[2];
-                    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
-                    #pragma unroll
-                    for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-                    *reinterpret_cast<uint4*>(d.out + off) = w[0];
-                    *reinterpret_cast<uint4*>(d.out + off + d.plane) = w[1];
-                    if (p.head_out) {
-                        #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float2 rb = __bfloat1622float2(h[i]);
-                            head_acc += rb.x * p.head_w[ch0 + 2 * i] + rb.y * p.head_w[ch0 + 2 * i + 1];
+                        for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+                        *reinterpret_cast<uint4*>(d.out + off) = w[0];
+                        *reinterpret_cast<uint4*>(d.out + off + d.plane) = w[1];
+                        if (p.head_out) {
+                            #pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float2 rb = __bfloat1622float2(h[i]);
+                                head_acc += rb.x * p.head_w[ch0 + 2 * i] + rb.y * p.head_w[ch0 + 2 * i + 1];
+                            }
                         }
                     }
+                    if (p.head_out) p.head_out[vox] = head_acc + *p.head_b;
                 }
-                if (p.head_out) p.head_out[vox] = head_acc + *p.head_b;
             }
+            // this warp's reads of the buffer are complete: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + 8u * buf);
         }
     }
     tc_fence_before();
@@ -546,14 +641,30 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     }
 }
 
-cudaError_t launch_rows(const RowsParams& p, int grid_m, int grid_n, size_t smem, cudaStream_t s) {
+cudaError_t launch_rows(const RowsParams& p, int grid_n, size_t smem, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    rows_kernel<<<dim3(grid_m, grid_n), kThreads, smem, s>>>(p);
+    // resident CTAs per SM: the occupancy query's answer, at most 512 / ncols
+    // by TMEM (a CTA beyond that would wait in tcgen05.alloc for a whole
+    // persistent CTA).  The grid is `persistent` times that many CTAs per SM:
+    // tiles are claimed dynamically, so a surplus CTA finds none and exits.
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rows_kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int by_tmem = 512 / (int)tmem_cols(p.nbuf * p.mt * p.n_tile);
+    const int per_sm = occ < by_tmem ? occ : by_tmem;
+    long long grid_m = (long long)sms * (per_sm > 0 ? per_sm : 1) * (p.persistent > 0 ? p.persistent : 1);
+    if (grid_m > p.tiles || !p.persistent) grid_m = p.tiles;
+    rows_kernel<<<dim3((unsigned)grid_m, grid_n), kThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

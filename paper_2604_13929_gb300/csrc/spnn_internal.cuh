@@ -88,6 +88,10 @@ struct RowsParams {
     int mt;                         // 128-row subtiles per CTA, stacked along y (halo mode), else 1
     TileGrid g;                     // CTA boxes: 128 * mt voxels each
     int n_tile, n_total, ksteps, stages;
+    int tiles;                      // CTA boxes of the grid; persistent CTAs claim them in order
+    int* tile_ctr;                  // [grid_n] claim counters, zero at launch
+    int persistent;                 // k >= 1: k x SMs x resident CTAs; 0: one CTA per tile
+    int nbuf;                       // TMEM accumulator buffers (2: epilogue overlaps the next tile)
     uint32_t a_stage_bytes, b_stage_bytes, stage_bytes;
     uint32_t idesc;
     int scatter_up, cout_up, split;
@@ -140,7 +144,9 @@ struct WgradHaloParams {
     int* err;
 };
 
-cudaError_t launch_rows(const RowsParams& p, int grid_m, int grid_n, size_t smem, cudaStream_t s);
+// Persistent launch: min(tiles, persistent x SMs x resident CTAs) x grid_n CTAs.
+constexpr int kMaxGridN = 16;               // N tiles of one rows GEMM (claim counters per launch)
+cudaError_t launch_rows(const RowsParams& p, int grid_n, size_t smem, cudaStream_t s);
 cudaError_t launch_wgrad_halo(const WgradHaloParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_wgrad(const WgradParams& p, dim3 grid, size_t smem, cudaStream_t s);
 // TMEM columns to allocate for n FP32 accumulator columns (a power of two >= 32).

@@ -138,7 +138,8 @@ def spnn_status(stream=None):
     _check(load().spnn_status(_stream(stream)))
 
 
-OPT = {"conv_subtiles": 1, "conv_planes": 2, "stage_kb": 3, "wgrad_halo": 4, "conv_full_halo": 5}
+OPT = {"conv_subtiles": 1, "conv_planes": 2, "stage_kb": 3, "wgrad_halo": 4, "conv_full_halo": 5,
+       "rows_persistent": 7}
 
 
 def spnn_set_option(key, value: int):
