@@ -64,8 +64,11 @@ int spnn_status(void* stream);
  *                           stacked along y, sharing one halo box and weight copy
  *   SPNN_OPT_CONV_PLANES    8-channel chunk planes per conv3 K-step (2, 4)
  *   SPNN_OPT_STAGE_KB       shared-memory budget of the stage ring in KB (<= 220)
- *   SPNN_OPT_WGRAD_HALO     1 (default): conv3 weight gradients on halo K-steps
- *                           where they fit; 0: always the per-tap kernel
+ *   SPNN_OPT_WGRAD_HALO     1 (default): conv3 weight gradients with at most 32
+ *                           output channels on halo K-steps (one input box and
+ *                           three shifted output-gradient boxes per x-run);
+ *                           2: wherever they fit (up to 80 output channels);
+ *                           0: always the per-tap kernel
  *   SPNN_OPT_CONV_FULL_HALO 1: conv3 forward / input gradient on 8 x 16 tiles whose
  *                           one box per plane block serves all 27 taps, where it
  *                           fits; 0 (default): one box per x-shift

@@ -537,61 +537,81 @@ int layer_dgrad(int kind, int B, int D, int H, int W, const void* dy, int cout, 
 // SPNN_OK, or 1 when the layer does not fit the halo scheme (caller falls back).
 int wgrad_halo(int B, int D, int H, int W, const void* x0, int c0, const void* x1, int c1, const void* dy,
                int cout, float* dw, float* db, cudaStream_t st) {
-    const int kc0 = c0 / 8, kc1 = c1 / 8, kc = kc0 + kc1;
-    const int nM = (9 * kc + 1 + 15) / 16;
-    // 16-voxel x-runs; the second source's box must land 128-byte aligned
-    // (kc0 * 2592 bytes); every accumulator tile must fit the 512 TMEM columns
-    if (W < 16 || W % 16 || (kc1 && kc0 % 4) || 3 * nM * cout > 512 || cout > 256) return 1;
+    const int kc0 = c0 / 8, kc1 = c1 / 8;
+    // x-runs of 16 or 32 voxels; one MMA of N = 3 cout <= 256; a CTA's planes np give
+    // 9 np + 1 row groups in nM tiles of 16 with nM * 3 cout <= 512 TMEM columns
+    if (W < 16 || W % 16 || 3 * cout > 256) return 1;
+    // automatic use only where it measured faster than the per-tap kernel
+    // (cout 32: 1.2 - 1.6x; cout 64: 0.8x); SPNN_OPT_WGRAD_HALO 2 forces it
+    if (g_opt_wgrad_halo < 2 && cout > 32) return 1;
+    const int nm_max = 512 / (3 * cout), np_max = (16 * nm_max - 1) / 9;
+    if (np_max < 1) return 1;
     WgradHaloParams p;
     memset(&p, 0, sizeof p);
     p.kc0 = kc0;
     p.kc1 = kc1;
     p.n = cout;
-    p.nM = nM;
     p.dw = dw;
     p.db = db;
+    // per source: the fewest splits of at most np_max planes, balanced
+    const int sp0 = (kc0 + np_max - 1) / np_max, sp1 = kc1 ? (kc1 + np_max - 1) / np_max : 0;
+    p.npc0 = (kc0 + sp0 - 1) / sp0;
+    p.npc1 = kc1 ? (kc1 + sp1 - 1) / sp1 : 0;
+    p.splits0 = sp0;
+    const int splits = sp0 + sp1;
+    p.ones_split = db ? splits - 1 : -1;
+    const int np_big = p.npc0 > p.npc1 ? p.npc0 : p.npc1;
+    const int nM = (9 * np_big + 16) / 16;
     p.g.B = B, p.g.D = D, p.g.H = H, p.g.W = W;
-    p.g.bx = 16, p.g.by = 1, p.g.bz = 1, p.g.bb = 1;
-    p.g.nx = W / 16, p.g.ny = H, p.g.nz = D;
+    // resident CTAs per SM by TMEM columns; runs of 32 voxels (512-byte TMA
+    // rows, the longest a box row holds) when two share an SM (measured faster
+    // there, slower with one CTA per SM)
+    const int per_sm = 512 / (int)tmem_cols(nM * 3 * cout);
+    p.rl = per_sm > 1 && W % 32 == 0 ? 32 : 16;
+    p.nx = W / p.rl;
+    p.zs = D % 8 == 0 ? 8 : (D % 4 == 0 ? 4 : (D % 2 == 0 ? 2 : 1));
+    p.nzs = D / p.zs;
     int rc;
     const cuuint64_t row = 16ull * W;
-    auto halo_map = [&](CUtensorMap* m, const void* ptr, int C) {
+    auto halo_map = [&](CUtensorMap* m, const void* ptr, int C, int planes) {
         cuuint64_t dims[5] = {8ull * W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B, (cuuint64_t)(C / 8)};
         cuuint64_t strides[4] = {row, row * H, row * H * D, row * H * D * B};
-        cuuint32_t box[5] = {8 * 18, 3, 3, 1, (cuuint32_t)(C / 8)};
+        cuuint32_t box[5] = {8u * p.rl, 3, 3, 1, (cuuint32_t)planes};
         return encode(m, ptr, dims, strides, box);
     };
-    if ((rc = halo_map(&p.amaps[0], x0, c0))) return rc;
-    if (c1 && (rc = halo_map(&p.amaps[1], x1, c1))) return rc;
+    if ((rc = halo_map(&p.amaps[0], x0, c0, p.npc0))) return rc;
+    if (c1 && (rc = halo_map(&p.amaps[1], x1, c1, p.npc1))) return rc;
     {
         cuuint64_t dims[5] = {8ull * W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B, (cuuint64_t)(cout / 8)};
         cuuint64_t strides[4] = {row, row * H, row * H * D, row * H * D * B};
-        cuuint32_t box[5] = {8 * 16, 1, 1, 1, (cuuint32_t)(cout / 8)};
+        cuuint32_t box[5] = {8u * p.rl, 1, 1, 1, (cuuint32_t)(cout / 8)};
         if ((rc = encode(&p.bmap, dy, dims, strides, box))) return rc;
     }
-    p.ksteps_total = (int)n_tiles(p.g);
-    // A region: every row a tile can read, (16 nM + 1) rows of 288 bytes
-    p.a_region = ((uint32_t)(16 * nM + 1) * 288u + 1023u) & ~1023u;
-    p.b_stage_bytes = (uint32_t)cout * 32u;
-    // resident CTAs per SM: TMEM columns, then the shared-memory ring
-    const int ncols = (int)tmem_cols(3 * nM * cout);
-    const int per_sm = 512 / ncols;
-    // with one CTA per SM, two K-steps per stage (one barrier handshake per 2 x 3 nM
-    // MMAs) measured 8-10 % faster; with two CTAs per SM the halved ring lost
+    p.ksteps_total = B * D * H * p.nx;
+    // A region: the rows of nM tiles (one run per row group), then three dY boxes
+    const uint32_t run = 16u * (uint32_t)p.rl;
+    p.a_region = ((uint32_t)(16 * nM) * run + 1023u) & ~1023u;
+    p.b_stage_bytes = 3u * (uint32_t)(cout / 8) * run;
+    // with one CTA per SM two K-steps per stage halve the barrier handshakes
     p.ksub = per_sm > 1 ? 1 : 2;
     p.sub_bytes = (p.a_region + p.b_stage_bytes + 1023u) & ~1023u;
     p.stage_bytes = (uint32_t)p.ksub * p.sub_bytes;
     int S = (int)((uint32_t)(per_sm > 1 ? 100 : 200) * 1024u / p.stage_bytes);
     p.stages = S < 2 ? 2 : (S > 8 ? 8 : S);
-    p.idesc = idesc_bf16(128, cout, 1, 1);
+    p.idesc = idesc_bf16(128, 3 * cout, 1, 1);
     p.err = err_ptr();
     if (!p.err) return fail(SPNN_ECUDA, "no device");
-    int grid = 152 * per_sm;
-    if (grid > p.ksteps_total) grid = p.ksteps_total;
-    p.ksteps_per_cta = (p.ksteps_total + grid - 1) / grid;
-    grid = (p.ksteps_total + p.ksteps_per_cta - 1) / p.ksteps_per_cta;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+    // K splits: about one CTA per resident slot over all plane splits
+    int gx = (sms * per_sm + splits - 1) / splits;
+    if (gx > p.ksteps_total) gx = p.ksteps_total;
+    p.ksteps_per_cta = (p.ksteps_total + gx - 1) / gx;
+    gx = (p.ksteps_total + p.ksteps_per_cta - 1) / p.ksteps_per_cta;
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + (2 * p.stages + 2) * 8;
-    cudaError_t e = launch_wgrad_halo(p, grid, smem, st);
+    e = launch_wgrad_halo(p, dim3(gx, splits), smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "wgrad_halo_kernel launch");
     return SPNN_OK;
 }
@@ -928,7 +948,7 @@ int spnn_set_option(int key, int value) {
         g_opt_stage_kb = value;
         return SPNN_OK;
     case SPNN_OPT_WGRAD_HALO:
-        g_opt_wgrad_halo = value != 0;
+        g_opt_wgrad_halo = value < 0 ? 0 : (value > 2 ? 2 : value);
         return SPNN_OK;
     case SPNN_OPT_CONV_FULL_HALO:
         g_opt_full_halo = value != 0;

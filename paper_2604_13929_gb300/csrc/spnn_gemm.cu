@@ -371,26 +371,27 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                 const uint32_t acc = tmem + buf * acc_cols;
                 int x0, y0, z0, b0;
                 tile_origin_u32(p.g, (uint32_t)t, x0, y0, z0, b0);
+                const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+                const int nch = p.n_tile / 16;
+                // up layers: column n = o n_up + channel, o = (oz, oy, ox) the fine offset
+                const long long fW = 2LL * p.g.W, fHW = fW * (2LL * p.g.H);
                 for (int m = 0; m < p.mt; ++m) {
                     int vx, vy, vz, vb;
                     const long long vox = row_voxel(p.g, x0, y0, z0, b0, m * kRows + r, &vx, &vy, &vz, &vb);
+                    // fine voxel (2 vx, 2 vy, 2 vz) of sample vb (up layers)
+                    const long long fine0 = ((long long)vb * (2 * p.g.D) + 2 * vz) * fHW + 2LL * vy * fW + 2 * vx;
                     float head_acc = 0.f;
-                    for (int j = 0; j < p.n_tile / 16; ++j) {
-                        uint32_t v[16];
-                        tmem_ld16(acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * p.n_tile + j * 16), v);
-                        tmem_wait_ld();
+                    // epilogue of accumulator chunk j (16 columns)
+                    auto emit = [&](int j, const uint32_t (&v)[16]) {
                         const int n0 = blockIdx.y * p.n_tile + j * 16;
                         const EpiDest& d = (n0 < p.split) ? p.d[0] : p.d[1];
-                        if (d.out == nullptr) continue;
+                        if (d.out == nullptr) return;
                         int ch0;
                         long long off;
                         if (p.scatter_up) {
                             const int o = n0 / p.cout_up;
-                            ch0 = n0 % p.cout_up;
-                            const int oz = o >> 2, oy = (o >> 1) & 1, ox = o & 1;
-                            const long long fine = (((long long)vb * (2 * p.g.D) + 2 * vz + oz) * (2 * p.g.H) + 2 * vy + oy) *
-                                                       (2LL * p.g.W) +
-                                                   2 * vx + ox;
+                            ch0 = n0 - o * p.cout_up;
+                            const long long fine = fine0 + (o >> 2) * fHW + ((o >> 1) & 1) * fW + (o & 1);
                             off = (ch0 >> 3) * d.plane + fine * 8;
                         } else {
                             ch0 = n0 - d.col0;
@@ -414,10 +415,10 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                             for (int i = 0; i < 16; ++i) f[i] = fmaxf(f[i], 0.f);
                         }
                         if (d.mask) {
-                            float m[16];
-                            load16_planes(d.mask + off, d.plane, m);
+                            float mk[16];
+                            load16_planes(d.mask + off, d.plane, mk);
                             #pragma unroll
-                            for (int i = 0; i < 16; ++i) f[i] = (m[i] > 0.f) ? f[i] : 0.f;
+                            for (int i = 0; i < 16; ++i) f[i] = (mk[i] > 0.f) ? f[i] : 0.f;
                         }
                         uint4 w[2];
                         __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
@@ -432,6 +433,12 @@ __global__ void __launch_bounds__(kThreads, 1) rows_kernel(const __grid_constant
                                 head_acc += rb.x * p.head_w[ch0 + 2 * i] + rb.y * p.head_w[ch0 + 2 * i + 1];
                             }
                         }
+                    };
+                    for (int j = 0; j < nch; ++j) {
+                        uint32_t v[16];
+                        tmem_ld16(acc + lane_base + (uint32_t)(m * p.n_tile + j * 16), v);
+                        tmem_wait_ld();
+                        emit(j, v);
                     }
                     if (p.head_out) p.head_out[vox] = head_acc + *p.head_b;
                 }
@@ -683,36 +690,35 @@ cudaError_t launch_wgrad(const WgradParams& p, dim3 grid, size_t smem, cudaStrea
 
 namespace spnn {
 
-constexpr uint32_t kHaloRow = 18 * 16;   // bytes of one halo row: 16 voxels + 2 halo, 16 B each
-
-// The 3 nM MMAs of one halo weight-gradient K-step: accumulator (dx, row block
-// j) at columns (dx nM + j) n; dx is a 1-unit (16-byte) start offset of A,
-// row block j starts 16 rows (kHaloRow units) further.  Unrolled for the
-// common nM so that the MMAs issue back to back.
-template <int NM>
-__device__ __forceinline__ void issue_wgrad_halo_step(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t n,
-                                                      uint32_t idesc, uint32_t acc) {
-#pragma unroll
-    for (int dxi = 0; dxi < 3; ++dxi)
-#pragma unroll
-        for (int j = 0; j < NM; ++j)
-            umma_bf16(tmem + (uint32_t)(dxi * NM + j) * n, ad + (uint32_t)(dxi + j * kHaloRow), bd, idesc, acc);
-}
-
-__device__ __forceinline__ void issue_wgrad_halo_step(int nM, uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t n,
-                                                      uint32_t idesc, uint32_t acc) {
-    switch (nM) {
-    case 1: issue_wgrad_halo_step<1>(tmem, ad, bd, n, idesc, acc); break;
-    case 2: issue_wgrad_halo_step<2>(tmem, ad, bd, n, idesc, acc); break;
-    case 3: issue_wgrad_halo_step<3>(tmem, ad, bd, n, idesc, acc); break;
-    case 4: issue_wgrad_halo_step<4>(tmem, ad, bd, n, idesc, acc); break;
-    case 5: issue_wgrad_halo_step<5>(tmem, ad, bd, n, idesc, acc); break;
-    default:
-        for (int dxi = 0; dxi < 3; ++dxi)
-            for (int j = 0; j < nM; ++j)
-                umma_bf16(tmem + (uint32_t)(dxi * nM + j) * n, ad + (uint32_t)(dxi + j * kHaloRow), bd, idesc, acc);
+// K-step walk of the halo weight gradient: x-runs of rl voxels fastest, then z
+// within a slab of zs planes, then y, then the slab, then the sample, so that
+// the (dz, dy) halo rows a K-step loads were loaded by a recent K-step (L2).
+struct HaloWalk {
+    int xr, zi, y, zsl, b;
+    __device__ __forceinline__ void start(const WgradHaloParams& p, int k) {
+        xr = k % p.nx;
+        k /= p.nx;
+        zi = k % p.zs;
+        k /= p.zs;
+        y = k % p.g.H;
+        k /= p.g.H;
+        zsl = k % p.nzs;
+        b = k / p.nzs;
     }
-}
+    __device__ __forceinline__ void next(const WgradHaloParams& p) {
+        if (++xr < p.nx) return;
+        xr = 0;
+        if (++zi < p.zs) return;
+        zi = 0;
+        if (++y < p.g.H) return;
+        y = 0;
+        if (++zsl < p.nzs) return;
+        zsl = 0;
+        ++b;
+    }
+    __device__ __forceinline__ int x0(const WgradHaloParams& p) const { return p.rl * xr; }
+    __device__ __forceinline__ int z0(const WgradHaloParams& p) const { return zsl * p.zs + zi; }
+};
 
 __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_constant__ WgradHaloParams p) {
     extern __shared__ uint8_t smem_raw[];
@@ -724,17 +730,27 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t done = bar0 + 16u * S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kc = p.kc0 + p.kc1;
-    const int groups = 9 * kc;                       // real row groups; group `groups` is the ones row
-    const uint32_t ncols = tmem_cols(3 * p.nM * p.n);
     const int kbeg = blockIdx.x * p.ksteps_per_cta;
     const int kend = min(kbeg + p.ksteps_per_cta, p.ksteps_total);
+    // this CTA's planes: npc planes of one source from plane `first` on (planes
+    // past the source's end load as zeros), `real` of them inside the source
+    const int split = blockIdx.y;
+    const int src = split < p.splits0 ? 0 : 1;
+    const int npc = src ? p.npc1 : p.npc0;
+    const int first = (src ? split - p.splits0 : split) * npc;
+    const int real = min(npc, (src ? p.kc1 : p.kc0) - first);
+    const int plane_off = (src ? p.kc0 : 0) + first;       // in the concatenated input
+    const int groups = 9 * npc;                            // row group `groups` is the ones row
+    const int nM = (groups + 16) / 16;                     // 128-row tiles holding groups + 1
+    const uint32_t n3 = 3u * (uint32_t)p.n;                 // MMA N: (dx, output channel)
+    const uint32_t ncols = tmem_cols(nM * (int)n3);
+    const uint32_t row = 16u * (uint32_t)p.rl;             // bytes of one run of one chunk plane
 
     // the ones row of every K-step region of every stage (written once; TMA never writes it)
     for (int s = 0; s < S * p.ksub; ++s) {
         uint32_t* dst = reinterpret_cast<uint32_t*>(smem + (size_t)(s / p.ksub) * p.stage_bytes +
-                                                    (size_t)(s % p.ksub) * p.sub_bytes + (size_t)groups * kHaloRow);
-        for (int i = threadIdx.x; i < (int)(kHaloRow / 4); i += blockDim.x) dst[i] = 0x3F803F80u;
+                                                    (size_t)(s % p.ksub) * p.sub_bytes + (size_t)groups * row);
+        for (int i = threadIdx.x; i < (int)(row / 4); i += blockDim.x) dst[i] = 0x3F803F80u;
     }
     fence_async_shared();
     if (threadIdx.x == 0) {
@@ -757,10 +773,11 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
     if (warp == 0) {
         // the whole warp walks the K-steps; one elected lane issues (see rows_kernel)
         const bool leader = elect_one();
-        const uint32_t tx = (uint32_t)kc * 9u * kHaloRow + p.b_stage_bytes;
+        const uint32_t b_box = (uint32_t)(p.n / 8) * row;   // n/8 planes of one run
+        const uint32_t tx = (uint32_t)groups * row + 3u * b_box;
         Ring q;
-        int x0, y0, z0, b0;
-        tile_origin(p.g, kbeg, x0, y0, z0, b0);
+        HaloWalk w;
+        w.start(p, kbeg);
         // a stage holds ns <= ksub consecutive K-steps
         for (int k = kbeg; k < kend; q.next(S)) {
             const int ns = min(p.ksub, kend - k);
@@ -772,14 +789,16 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
                 break;
             }
             if (leader) mbar_expect_tx(full, (uint32_t)ns * tx);
-            for (int j = 0; j < ns; ++j, tile_next(p.g, x0, y0, z0, b0)) {
+            for (int j = 0; j < ns; ++j, w.next(p)) {
                 const uint32_t a_dst = sbase + (uint32_t)s * p.stage_bytes + (uint32_t)j * p.sub_bytes;
                 if (leader) {
-                    tma_load_5d(a_dst, &p.amaps[0], full, 8 * (x0 - 1), y0 - 1, z0 - 1, b0, 0);
-                    if (p.kc1)
-                        tma_load_5d(a_dst + (uint32_t)p.kc0 * 9u * kHaloRow, &p.amaps[1], full, 8 * (x0 - 1),
-                                    y0 - 1, z0 - 1, b0, 0);
-                    tma_load_5d(a_dst + p.a_region, &p.bmap, full, 8 * x0, y0, z0, b0, 0);
+                    const int x0 = w.x0(p), z0 = w.z0(p);
+                    // input: (rl, 3, 3) voxels of npc planes, rows (plane, dz, dy)
+                    tma_load_5d(a_dst, &p.amaps[src], full, 8 * x0, w.y - 1, z0 - 1, w.b, first);
+                    // output gradient shifted by -dx: B block dxi holds dY at x - (dxi - 1)
+                    for (int dxi = 0; dxi < 3; ++dxi)
+                        tma_load_5d(a_dst + p.a_region + (uint32_t)dxi * b_box, &p.bmap, full, 8 * (x0 + 1 - dxi),
+                                    w.y, z0, w.b, 0);
                 }
             }
             k += ns;
@@ -800,10 +819,16 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
             tc_fence_after();
             for (int j = 0; j < ns; ++j) {
                 const uint32_t a0 = sbase + (uint32_t)s * p.stage_bytes + (uint32_t)j * p.sub_bytes;
-                const uint64_t bd = smem_desc(a0 + p.a_region, 128u, 256u);
-                const uint64_t ad = smem_desc(a0, 128u, kHaloRow);
+                // MN-major operands: 8-voxel core matrices 128 bytes apart along K,
+                // 8-channel groups one run apart along M / N; K-block kb = voxels
+                // 16 kb .. 16 kb + 15 of the run, a 256-byte start offset
                 if (leader)
-                    issue_wgrad_halo_step(p.nM, tmem, ad, bd, (uint32_t)p.n, p.idesc, (k > kbeg || j > 0) ? 1u : 0u);
+                    for (int kb = 0; kb < p.rl / 16; ++kb) {
+                        const uint64_t bd = smem_desc(a0 + p.a_region + 256u * kb, 128u, row);
+                        for (int m = 0; m < nM; ++m)
+                            umma_bf16(tmem + (uint32_t)m * n3, smem_desc(a0 + (uint32_t)m * 16u * row + 256u * kb, 128u, row),
+                                      bd, p.idesc, (k > kbeg || j > 0 || kb > 0) ? 1u : 0u);
+                    }
             }
             if (leader) umma_commit(bar0 + 8u * (S + s));
             k += ns;
@@ -820,28 +845,28 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
             if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
         } else if (kend > kbeg) {
             tc_fence_after();
-            const int ci_all = 8 * kc;
-            for (int dxi = 0; dxi < 3; ++dxi)
-                for (int j = 0; j < p.nM; ++j) {
-                    const int g = 16 * j + (r >> 3), r8 = r & 7;
+            const int ci_all = 8 * (p.kc0 + p.kc1);
+            for (int m = 0; m < nM; ++m) {
+                const int g = 16 * m + (r >> 3), r8 = r & 7;
+                const int pl = g / 9, t9 = g % 9;             // t9 = (dz + 1) * 3 + (dy + 1)
+                const bool wrow = g < groups && pl < real;
+                const bool orow = g == groups && r8 == 0 && split == p.ones_split;
+                for (uint32_t c = 0; c < n3; c += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)m * n3 + c, v);
+                    tmem_wait_ld();
+                    const int dxi = (int)c / p.n, co = (int)c % p.n;
                     float* dst = nullptr;
-                    if (g < groups) {
-                        const int c8 = g / 9, t9 = g % 9;   // t9 = (dz + 1) * 3 + (dy + 1)
-                        const int tap = t9 * 3 + dxi;       // (dz+1)*9 + (dy+1)*3 + (dx+1)
-                        dst = p.dw + ((size_t)tap * ci_all + c8 * 8 + r8) * p.n;
-                    } else if (g == groups && dxi == 1 && r8 == 0) {
-                        dst = p.db;
-                    }
-                    for (int c = 0; c < p.n / 16; ++c) {
-                        uint32_t v[16];
-                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((dxi * p.nM + j) * p.n + c * 16), v);
-                        tmem_wait_ld();
-                        if (dst) {
+                    if (wrow)
+                        dst = p.dw + ((size_t)(t9 * 3 + dxi) * ci_all + (plane_off + pl) * 8 + r8) * p.n + co;
+                    else if (orow && dxi == 1)
+                        dst = p.db + co;
+                    if (dst) {
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) atomicAdd(dst + c * 16 + e, __uint_as_float(v[e]));
-                        }
+                        for (int e = 0; e < 16; ++e) atomicAdd(dst + e, __uint_as_float(v[e]));
                     }
                 }
+            }
         }
     }
     tc_fence_before();
@@ -852,7 +877,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_halo_kernel(const __grid_co
     }
 }
 
-cudaError_t launch_wgrad_halo(const WgradHaloParams& p, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_wgrad_halo(const WgradHaloParams& p, dim3 grid, size_t smem, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e =

@@ -123,18 +123,26 @@ struct WgradParams {
     int* err;
 };
 
-// conv3 weight gradient with halo K-steps: each K-step is one x-run of 16
-// output voxels; one TMA box per source brings (18 x 3 x 3) voxels of every
-// input chunk plane, laid out [plane][z][y][x] with 288-byte rows, so the
-// row groups (plane, dz, dy) sit at a uniform 288-byte stride and dx is a
-// 16-byte start offset: all 27 taps from one box.  Row group 9 * kc_total is
-// a row of ones (bias gradient, counted for dx = 0 only).  A CTA accumulates
-// 3 x nM tiles (x-shift, 16 groups) of n columns in TMEM over its K range.
+// conv3 weight gradient with halo K-steps: dW[tap][ci][co] = sum_v
+// X[v + tap][ci] dY[v][co], summed as sum_u X[u][ci] dY[u - d][co].  Each
+// K-step is one x-run of rl (16 or 32) voxels u.  A (MN-major): one TMA box of
+// the input, (rl x 3 x 3) voxels of npc chunk planes laid out [plane][dz][dy][x],
+// so the row groups (plane, dz, dy) sit one run (16 rl bytes) apart; row group
+// 9 npc is a row of ones (bias gradient).  B (MN-major): three boxes of dY, at x - dx for dx =
+// -1, 0, 1, side by side, so one MMA has N = 3 n columns (dx, co) and no
+// operand needs an x-halo.  blockIdx.y splits the planes (npc per CTA, within
+// one source; ceil((9 npc + 1) / 16) 128-row tiles each), blockIdx.x the K-steps, which walk
+// x-runs, then z within a slab of zs planes, then y, then slabs, then samples.
 struct WgradHaloParams {
-    CUtensorMap amaps[2];           // chunk-plane maps of the sources, box (8*18, 3, 3, 1, planes)
-    CUtensorMap bmap;               // output gradient, box (8*16, 1, 1, 1, n/8)
-    int kc0, kc1, n, nM;
-    TileGrid g;                     // 16-voxel x-runs of the grid
+    CUtensorMap amaps[2];           // chunk-plane maps of the sources, box (8 rl, 3, 3, 1, npc0 / npc1)
+    CUtensorMap bmap;               // output gradient, box (8 rl, 1, 1, 1, n/8)
+    int rl;                         // voxels per x-run (K-step)
+    int kc0, kc1, n;
+    int npc0, npc1;                 // planes per CTA of source 0 / 1
+    int splits0;                    // plane splits over source 0 (the rest cover source 1)
+    int ones_split;                 // split whose ones row gives the bias gradient (-1: none)
+    int nx, zs, nzs;                // x-runs per row, z slab depth, slabs per sample
+    TileGrid g;                     // B, D, H, W of the layer
     int ksteps_total, ksteps_per_cta, stages;
     int ksub;                       // K-steps per stage (each its own a_region + B block, sub_bytes apart)
     uint32_t a_region, b_stage_bytes, sub_bytes, stage_bytes;
@@ -147,7 +155,7 @@ struct WgradHaloParams {
 // Persistent launch: min(tiles, persistent x SMs x resident CTAs) x grid_n CTAs.
 constexpr int kMaxGridN = 16;               // N tiles of one rows GEMM (claim counters per launch)
 cudaError_t launch_rows(const RowsParams& p, int grid_n, size_t smem, cudaStream_t s);
-cudaError_t launch_wgrad_halo(const WgradHaloParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_wgrad_halo(const WgradHaloParams& p, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t launch_wgrad(const WgradParams& p, dim3 grid, size_t smem, cudaStream_t s);
 // TMEM columns to allocate for n FP32 accumulator columns (a power of two >= 32).
 __host__ __device__ inline uint32_t tmem_cols(int n) {

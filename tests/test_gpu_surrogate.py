@@ -391,12 +391,18 @@ def test_conv3_tilings_agree_with_oracle(S, subtiles, planes):
     check(np.concatenate([f64(dx0), f64(dx1)], axis=-1), g, ga, what="dgrad")
 
 
-# input channels 16 .. 80 give 2 .. 6 row blocks of 16 (tap, 8-channel) groups per x-shift
+# (plane, dz, dy) row groups of 2 .. 10 planes per CTA, one or two sources, and
+# plane splits across CTAs (co = 64: at most 3 planes per CTA, so 64 channels
+# split 3 + 3 + 2, the last CTA's box running one zero plane past the source);
+# halo 2 forces the halo kernel where the automatic choice takes the per-tap one,
+# and 16 + 16 -> 32 runs 32-voxel x-runs (two CTAs per SM) over two sources
 @pytest.mark.parametrize("c0,c1,co,halo", [(32, 0, 32, 1), (32, 32, 32, 1), (16, 0, 32, 1), (32, 32, 32, 0),
-                                           (48, 0, 32, 1), (80, 0, 16, 1)])
+                                           (48, 0, 32, 1), (80, 0, 16, 1), (64, 0, 64, 2), (40, 24, 64, 2),
+                                           (32, 0, 80, 2), (64, 64, 64, 2), (16, 16, 32, 1)])
 def test_conv3_wgrad_halo_kernel(S, c0, c1, co, halo):
     """conv3 weight and bias gradients with halo K-steps (all 27 taps from one
-    box per 16-voxel row) and with the per-tap kernel, against the oracle."""
+    input box and three shifted output-gradient boxes per 16-voxel run) and
+    with the per-tap kernel, against the oracle."""
     rng = np.random.default_rng(14)
     B, D, H, W = 2, 4, 8, 32
     x0 = bf(rnd(rng, (B, D, H, W, c0)))
@@ -413,6 +419,25 @@ def test_conv3_wgrad_halo_kernel(S, c0, c1, co, halo):
         S.spnn_status()
     finally:
         S.spnn_set_option("wgrad_halo", 1)
+    check(dw.cpu().numpy().astype(np.float64), ref_w, abs_w, out_bf16=False, what="dw")
+    check(db.cpu().numpy().astype(np.float64), ref_b, abs_b, out_bf16=False, what="db")
+
+
+@pytest.mark.parametrize("B,D,H,W", [(1, 2, 4, 64), (1, 16, 4, 16), (3, 1, 8, 32)])
+def test_conv3_wgrad_halo_walks(S, B, D, H, W):
+    """The halo weight gradient's K walk (x-runs, z within slabs of up to 8
+    planes, y, slabs, samples): slabs of 2, two slabs of 8, slabs of 1 over
+    several samples, four x-runs per row."""
+    rng = np.random.default_rng(B * 100 + D)
+    c0, co = 32, 32
+    x0 = bf(rnd(rng, (B, D, H, W, c0)))
+    dy = bf(rnd(rng, (B, D, H, W, co)))
+    ref_w, ref_b = U.conv3_wgrad(f64(x0), f64(dy))
+    abs_w, abs_b = U.conv3_wgrad(np.abs(f64(x0)), np.abs(f64(dy)))
+    dw = torch.zeros((27, c0, co), dtype=torch.float32, device="cuda")
+    db = torch.zeros(co, dtype=torch.float32, device="cuda")
+    S.spnn_layer_wgrad(S.CONV3, (B, D, H, W), x0, None, dy, dw, db)
+    S.spnn_status()
     check(dw.cpu().numpy().astype(np.float64), ref_w, abs_w, out_bf16=False, what="dw")
     check(db.cpu().numpy().astype(np.float64), ref_b, abs_b, out_bf16=False, what="db")
 
