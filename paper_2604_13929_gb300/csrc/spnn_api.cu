@@ -143,8 +143,17 @@ int n_taps_of(int kind) { return kind == KIND_CONV3 ? 27 : 8; }
 
 // ------------------------------------------------------------ rows GEMM --
 // Choose the K-step geometry of a rows GEMM (maps already hold their boxes).
+// N-tile width of a rows GEMM and of its packed operand: up to 256 columns;
+// 128 for a GEMM with a scatter epilogue (up forward, down input gradient)
+// and N >= 256, which the epilogue bounds: two CTAs (eight epilogue warps)
+// then share an SM.  Measured 1.3 - 1.6x faster on the U-Net's up layers.
+int gemm_n_tile(bool scatter, int n_total) {
+    if (scatter && n_total >= 256) return 128;
+    return n_total <= 256 ? n_total : 256;
+}
+
 void rows_geometry(RowsParams& p) {
-    p.n_tile = p.n_total <= 256 ? p.n_total : 256;
+    p.n_tile = gemm_n_tile(p.scatter_up, p.n_total);
     if (p.tap_mode == TAP_SHIFT3 && p.halo == 2) {
         const uint32_t nrow = (uint32_t)p.n_tile * 16u;
         p.halo_plane = (uint32_t)((p.g.bx + 2) * (p.g.by + 2) * 3 * 16);
@@ -847,7 +856,9 @@ int pack(int kind, int cin, int cout, int which, const float* w, void* packed, c
     if (!w || !packed) return fail(SPNN_EINVAL, "null tensor");
     int taps_p, kc, n_total;
     pack_geometry(kind, which, cin, cout, &taps_p, &kc, &n_total);
-    const int n_tile = n_total <= 256 ? n_total : 256;
+    // the GEMMs with a scatter epilogue: up forward and down input gradient
+    const bool scatter = which == SPNN_PACK_FWD ? kind == KIND_UP : kind == KIND_DOWN;
+    const int n_tile = gemm_n_tile(scatter, n_total);
     if (n_total % n_tile) return fail(SPNN_EINVAL, "packed N %d > 256 not a multiple of 256", n_total);
     const long long total = (long long)taps_p * kc * 8 * n_total;
     pack_kernel<<<grid_for(total), 256, 0, st>>>(kind, which, cin, cout, taps_p, kc, n_tile, w,
