@@ -1,6 +1,7 @@
 // spnn_api.cu -- C ABI of the fluence surrogate (include/spnn.h): tensor-map
 // construction, layer calls on the tensor-core GEMM kernels, weight packing,
 // data kernels and the U-Net runtime (buffers, forward, backward, Adam).
+#include <atomic>
 #include <cudaTypedefs.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -278,11 +279,11 @@ int rows_gemm(RowsParams& p, cudaStream_t st) {
     if (!p.err) return fail(SPNN_ECUDA, "no device");
     const int grid_n = p.n_total / p.n_tile;
     if (grid_n > kMaxGridN) return fail(SPNN_EINVAL, "GEMM N %d: more than %d N tiles", p.n_total, kMaxGridN);
-    static unsigned ctr_next = 0;
+    static std::atomic<unsigned> ctr_next{0};   // launches may come from several host threads
     void* ctr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ctr, g_tile_ctr);
     if (e != cudaSuccess) return cuda_fail(e, "tile counters");
-    p.tile_ctr = static_cast<int*>(ctr) + (size_t)(ctr_next++ % kCtrSlots) * kMaxGridN;
+    p.tile_ctr = static_cast<int*>(ctr) + (size_t)(ctr_next.fetch_add(1) % kCtrSlots) * kMaxGridN;
     e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int) * grid_n, st);
     if (e != cudaSuccess) return cuda_fail(e, "tile counter reset");
     // stages, alignment slack, 2 S + 12 mbarriers, four tile slots and the TMEM address slot

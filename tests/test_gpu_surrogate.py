@@ -423,6 +423,37 @@ def test_conv3_wgrad_halo_kernel(S, c0, c1, co, halo):
     check(db.cpu().numpy().astype(np.float64), ref_b, abs_b, out_bf16=False, what="db")
 
 
+def test_rows_gemm_persistent_grid_sizes_agree(S):
+    """The persistent rows GEMM claims tiles dynamically; the result of every
+    tile is independent of the CTA that computes it, so grids of one CTA per
+    tile and of 1, 2 or 3 times the resident CTAs give identical bits (conv3
+    forward with concatenated input and bias, and the down layer's scatter
+    input gradient with 128-column N tiles)."""
+    rng = np.random.default_rng(31)
+    B, D, H, W, c0, c1, co = 2, 8, 16, 32, 16, 16, 32
+    x0 = bf(rnd(rng, (B, D, H, W, c0)))
+    x1 = bf(rnd(rng, (B, D, H, W, c1)))
+    pk = packed(S, S.CONV3, c0 + c1, co, 0, rnd(rng, (27, c0 + c1, co), 0.1))
+    bias = torch.tensor(rnd(rng, co, 0.5), dtype=torch.float32, device="cuda")
+    dy = bf(rnd(rng, (B, D // 2, H // 2, W // 2, 64)))
+    pkd = packed(S, S.DOWN, 32, 64, 1, rnd(rng, (8, 32, 64), 0.1))
+    outs = []
+    try:
+        for grid in (0, 1, 2, 3):
+            S.spnn_set_option("rows_persistent", grid)
+            y = zeros_act(B, D, H, W, co)
+            S.spnn_layer_forward(S.CONV3, (B, D, H, W), x0, x1, pk, bias, co, True, y)
+            dx = zeros_act(B, D, H, W, 32)
+            S.spnn_layer_dgrad(S.DOWN, (B, D, H, W), dy, pkd, 32, 0, dx)
+            S.spnn_status()
+            outs.append((y.clone(), dx.clone()))
+    finally:
+        S.spnn_set_option("rows_persistent", 2)
+    for y, dx in outs[1:]:
+        assert torch.equal(y, outs[0][0]) and torch.equal(dx, outs[0][1])
+    assert float(outs[0][0].float().abs().sum()) > 0 and float(outs[0][1].float().abs().sum()) > 0
+
+
 @pytest.mark.parametrize("B,D,H,W", [(1, 2, 4, 64), (1, 16, 4, 16), (3, 1, 8, 32)])
 def test_conv3_wgrad_halo_walks(S, B, D, H, W):
     """The halo weight gradient's K walk (x-runs, z within slabs of up to 8
