@@ -26,6 +26,12 @@
  * (SPNN_OK) or a negative SPNN_E* code; spnn_last_error() gives a
  * thread-local message.  There is no CPU path: without a GPU every call
  * returns SPNN_ECUDA.
+ *
+ * Concurrency: a forward or input-gradient GEMM (spnn_layer_forward,
+ * spnn_layer_dgrad and the network calls built on them) zeroes one of 64
+ * device tile counters on its stream before its launch, taken in turn; calls
+ * may run concurrently on different streams as long as fewer than 64 of them
+ * are in flight at once.
  */
 #ifndef SPNN_H
 #define SPNN_H
@@ -72,7 +78,7 @@ int spnn_status(void* stream);
  *   SPNN_OPT_CONV_FULL_HALO 1: conv3 forward / input gradient on 8 x 16 tiles whose
  *                           one box per plane block serves all 27 taps, where it
  *                           fits; 0 (default): one box per x-shift
- *   SPNN_OPT_ROWS_PERSISTENT k >= 1: forward / input-gradient GEMMs launch k
+ *   SPNN_OPT_ROWS_PERSISTENT k in 1..16: forward / input-gradient GEMMs launch k
  *                           CTAs per resident slot that the occupancy query
  *                           reports (default 2: the query has answered one CTA
  *                           per SM where two are resident), each claiming tiles

@@ -554,7 +554,13 @@ int wgrad_halo(int B, int D, int H, int W, const void* x0, int c0, const void* x
     // automatic use only where it measured faster than the per-tap kernel
     // (cout 32: 1.2 - 1.6x; cout 64: 0.8x); SPNN_OPT_WGRAD_HALO 2 forces it
     if (g_opt_wgrad_halo < 2 && cout > 32) return 1;
-    const int nm_max = 512 / (3 * cout), np_max = (16 * nm_max - 1) / 9;
+    // at most two 128-row tiles per CTA where that keeps its accumulators
+    // within 256 TMEM columns: two CTAs per SM keep twice the loads in flight
+    // (the kernel is latency-bound; 1.25x faster on the 64^3 32-channel layers
+    // than three tiles and one CTA per SM, despite the extra padded rows)
+    int nm_max = 512 / (3 * cout);
+    if (2 * 3 * cout <= 256 && nm_max > 2) nm_max = 2;
+    const int np_max = (16 * nm_max - 1) / 9;
     if (np_max < 1) return 1;
     WgradHaloParams p;
     memset(&p, 0, sizeof p);
@@ -960,13 +966,15 @@ int spnn_set_option(int key, int value) {
         g_opt_stage_kb = value;
         return SPNN_OK;
     case SPNN_OPT_WGRAD_HALO:
-        g_opt_wgrad_halo = value < 0 ? 0 : (value > 2 ? 2 : value);
+        if (value < 0 || value > 2) return fail(SPNN_EINVAL, "halo weight-gradient setting %d not in 0..2", value);
+        g_opt_wgrad_halo = value;
         return SPNN_OK;
     case SPNN_OPT_CONV_FULL_HALO:
         g_opt_full_halo = value != 0;
         return SPNN_OK;
     case SPNN_OPT_ROWS_PERSISTENT:
-        g_opt_rows_persistent = value < 0 ? 0 : value;
+        if (value < 0 || value > 16) return fail(SPNN_EINVAL, "persistent grid multiple %d not in 0..16", value);
+        g_opt_rows_persistent = value;
         return SPNN_OK;
     default:
         return fail(SPNN_EINVAL, "unknown option %d", key);
