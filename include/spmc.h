@@ -91,8 +91,11 @@ enum sp_option {
                                 warp vote, branch-free phases, all events in
                                 the compacted event phase); 0 the generic
                                 template kernel (same photons, same method) */
-    SP_OPT_STEPS_PER_PASS = 17 /* streamlined kernel: voxel steps a lane
+    SP_OPT_STEPS_PER_PASS = 17,/* streamlined kernel: voxel steps a lane
                                 takes per pass of its warp, [1, 64] (8);
+                                results do not depend on it                */
+    SP_OPT_BATCH_CHUNK = 18   /* batched one-launch mode, streamlined kernel:
+                                photons per warp claim, [32, 2^24] (2048);
                                 results do not depend on it                */
 };
 
@@ -240,8 +243,8 @@ size_t sp_mc_result_size(void);
  * (the batched pattern of the design sweeps; the paper runs its cases one at
  * a time).  Each problem has its own bit-packed mask, Q32.32 voxel field and
  * integer tallies, exactly as an sp_mc_create handle.  With the streamlined
- * kernel (SP_OPT_KERNEL = 1, default) every warp claims chunks of 2048
- * photons of one problem from a shared counter and keeps that problem's
+ * kernel (SP_OPT_KERNEL = 1, default) every warp claims chunks of
+ * SP_OPT_BATCH_CHUNK (2048) photons of one problem from a shared counter and keeps that problem's
  * tallies in shared memory until it moves on; with the generic kernel (0)
  * photons of all problems are claimed one by one, so lanes of a warp carry
  * different problems.  With the same seed and photon counts every problem's

@@ -1112,6 +1112,7 @@ extern "C" void sp_mc_batch_destroy(sp_mc_batch_t *b) {
 
 extern "C" int sp_mc_batch_set_option(sp_mc_batch_t *b, int key, double value) {
     if (!b) return fail(SP_EINVAL, "null batch");
+    if (!std::isfinite(value)) return fail(SP_EINVAL, "option value must be finite");
     switch (key) {
     case SP_OPT_THREADS: {
         const int t = (int)value;
@@ -1129,6 +1130,13 @@ extern "C" int sp_mc_batch_set_option(sp_mc_batch_t *b, int key, double value) {
     case SP_OPT_BATCH_MODE:
         if (value != 0 && value != 1) return fail(SP_EINVAL, "batch mode must be 0 or 1");
         b->mode = (int)value; return SP_OK;
+    case SP_OPT_BATCH_CHUNK:
+        if (value < 32 || value > (double)(1 << 24)) return fail(SP_EINVAL, "batch chunk must be in [32, 2^24]");
+        if ((u32)value != b->chunk) {
+            b->chunk = (u32)value;
+            b->table_valid = false;          // chunk indices of the problem table change
+        }
+        return SP_OK;
     case SP_OPT_KERNEL:
     case SP_OPT_STEPS_PER_PASS: {
         // the one-launch kernel's own setting, and every problem's for mode 1
@@ -1166,6 +1174,7 @@ extern "C" int sp_mc_batch_get_option(const sp_mc_batch_t *b, int key, double *v
     case SP_OPT_COMPACT: *value = b->compact_k; return SP_OK;
     case SP_OPT_GRAPH: *value = b->use_graph; return SP_OK;
     case SP_OPT_BATCH_MODE: *value = b->mode; return SP_OK;
+    case SP_OPT_BATCH_CHUNK: *value = b->chunk; return SP_OK;
     case SP_OPT_KERNEL: *value = b->variant; return SP_OK;
     case SP_OPT_STEPS_PER_PASS: *value = b->steps_per_pass; return SP_OK;
     default: return sp_mc_get_option(b->h[0], key, value);

@@ -29,7 +29,7 @@ NBATCH, NBIN, NHIST = 16, 64, 257
 OPT = {"path_cap": 1, "rr_weight": 2, "rr_mult": 3, "tally_field": 4, "precision": 5,
        "records": 6, "blocks": 7, "threads": 8, "iter_limit": 9, "smem_bricks": 10,
        "pid_offset": 11, "compact": 12, "graph": 13, "lateral_bc": 14, "batch_mode": 15,
-       "kernel": 16, "steps_per_pass": 17}
+       "kernel": 16, "steps_per_pass": 17, "batch_chunk": 18}
 ERR_NAMES = {SP_EINVAL: "SP_EINVAL", SP_ENOMEM: "SP_ENOMEM", SP_ECUDA: "SP_ECUDA",
              SP_ESTEPLIMIT: "SP_ESTEPLIMIT", SP_EOVERFLOW: "SP_EOVERFLOW"}
 

@@ -48,6 +48,18 @@ def _single(spmc, pr, n, seed, kernel=1):
     return t, f
 
 
+def _single_runs(spmc, pr, ns, seed):
+    """One handle running the photon counts ns in turn (ids continue)."""
+    sim = spmc.Simulation(pr[0], pr[1], pr[2], pr[3])
+    for n in ns:
+        if n:
+            sim.run(n, seed)
+    t = sim.tallies(check=False)
+    f = sim.raw_field()
+    sim.close()
+    return t, f
+
+
 def _assert_same(a, af, b, bf):
     for k in RAW:
         assert np.array_equal(a[k], b[k]), k
@@ -68,15 +80,31 @@ def test_batch_equals_separate_runs(spmc, problems, graph, mode, kernel):
             _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
 
 
-@pytest.mark.parametrize("steps_per_pass,threads", [(8, 128), (3, 256), (16, 64)])
-def test_one_launch_batch_is_independent_of_launch_shape(spmc, problems, steps_per_pass, threads):
-    """Chunks of 2048 photons per warp claim: problems far larger than one
-    chunk, warps changing problem many times, any launch shape."""
+@pytest.mark.parametrize("steps_per_pass,threads,chunk", [(8, 128, 2048), (3, 256, 32), (16, 64, 9000)])
+def test_one_launch_batch_is_independent_of_launch_shape(spmc, problems, steps_per_pass, threads, chunk):
+    """Chunks of photons per warp claim (2048 by default, down to one photon
+    per lane, and uneven sizes): problems far larger than one chunk, warps
+    changing problem many times, any launch shape."""
     n = [70000, 9000, 3000, 41000]
-    with spmc.Batch(problems, graph=0, batch_mode=0, steps_per_pass=steps_per_pass, threads=threads) as b:
+    with spmc.Batch(problems, graph=0, batch_mode=0, steps_per_pass=steps_per_pass, threads=threads,
+                    batch_chunk=chunk) as b:
         b.run(n, 123)
         for i, pr in enumerate(problems):
             ref, rf = _single(spmc, pr, n[i], 123)
+            _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
+
+
+def test_chunk_change_between_graph_replays(spmc, problems):
+    """Changing the claim size rebuilds the problem table and the captured
+    graph; the continued runs still equal separate runs of the same photons."""
+    n = [30000, 12000, 5000, 20000]
+    with spmc.Batch(problems, graph=1, batch_mode=0) as b:
+        b.run(n, 5)
+        b.set_option("batch_chunk", 700)
+        assert b.get_option("batch_chunk") == 700
+        b.run(n, 5)
+        for i, pr in enumerate(problems):
+            ref, rf = _single_runs(spmc, pr, [n[i], n[i]], 5)
             _assert_same(b.tallies(i), b.raw_field(i), ref, rf)
 
 
