@@ -21,7 +21,11 @@ Tensors are channels-last float64 arrays (B, D, H, W, C).
            tap index oz * 4 + oy * 2 + ox;  W: (8, Cin, Cout)
   up     transposed 2x2x2, stride 2:  y[2v + o] = b + x[v] @ W[o];  W: (8, Cin, Cout)
   head   p[v] = c + x[v] . h  (one output channel, float)
-  loss   mean over every voxel of every sample of (p - target)^2
+  loss   mean over every voxel of every sample of w (p - target)^2, with
+         w = 1 (plain), or, fluence-weighted, w = exp(target) divided by the
+         mean of exp(target) over the voxels of the same sample: the target
+         is a log fluence, so this weighs each voxel's log error by its
+         fluence, as Eq. RMSw weighs depth layers (weights average to 1)
 
 Network with base width c0 (widths c0, 2c0, 4c0, 8c0 on four levels):
 
@@ -195,15 +199,24 @@ def forward(params, x, c0: int):
     return _mm(act[prev], h[:, None])[..., 0] + c, act
 
 
-def loss(pred, target):
-    return float(np.mean((pred - target) ** 2))
+def loss_weights(target, fluence_weighted: bool = False):
+    """Per-voxel loss weights: ones, or exp(target) over its sample's mean."""
+    if not fluence_weighted:
+        return np.ones_like(target)
+    e = np.exp(target)
+    mean = e.reshape(e.shape[0], -1).mean(axis=1)
+    return e / mean.reshape((-1,) + (1,) * (target.ndim - 1))
 
 
-def backward(params, act, pred, target, c0: int):
+def loss(pred, target, fluence_weighted: bool = False):
+    return float(np.mean(loss_weights(target, fluence_weighted) * (pred - target) ** 2))
+
+
+def backward(params, act, pred, target, c0: int, fluence_weighted: bool = False):
     """Gradients of loss(pred, target) for every parameter, by the chain rule."""
     table = layer_table(c0, act["x"].shape[-1])
     n = pred.size
-    dp = 2.0 * (pred - target) / n
+    dp = 2.0 * loss_weights(target, fluence_weighted) * (pred - target) / n
     h, _ = params["head"]
     last = table[-1][0]
     grads = {"head": ((act[last] * dp[..., None]).reshape(-1, act[last].shape[-1]).sum(0),

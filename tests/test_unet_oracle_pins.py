@@ -130,16 +130,17 @@ def test_decoder_concatenation_order(rng):
     np.testing.assert_allclose(act["c0a"], ref, rtol=1e-12, atol=1e-12)
 
 
-def test_network_gradients_match_finite_differences(rng):
+@pytest.mark.parametrize("weighted", [False, True])
+def test_network_gradients_match_finite_differences(rng, weighted):
     c0 = 2
     P = U.init_params(c0, 5)
     x = rng.standard_normal((2, 16, 16, 16, U.N_FEATURES))
     target = rng.standard_normal((2, 16, 16, 16))
     pred, act = U.forward(P, x, c0)
-    grads = U.backward(P, act, pred, target, c0)
+    grads = U.backward(P, act, pred, target, c0, fluence_weighted=weighted)
 
     def loss_now():
-        return U.loss(U.forward(P, x, c0)[0], target)
+        return U.loss(U.forward(P, x, c0)[0], target, fluence_weighted=weighted)
 
     h = 1e-6
     checked = 0
@@ -159,6 +160,25 @@ def test_network_gradients_match_finite_differences(rng):
                 assert abs(fd - g[idx]) <= 1e-6 * abs(fd) + 1e-9, (name, which, idx, fd, g[idx])
                 checked += 1
     assert checked == 2 * 2 * 21
+
+
+def test_fluence_weights_definition(rng):
+    """Weights average to one per sample, are proportional to the fluence
+    exp(target) within a sample, reduce to ones for a constant target, and
+    make the loss the fluence-weighted mean of the squared log error."""
+    target = rng.standard_normal((3, 4, 5, 6)) * 2.0
+    w = U.loss_weights(target, True)
+    np.testing.assert_allclose(w.reshape(3, -1).mean(axis=1), 1.0, rtol=1e-12)
+    ratio = w / np.exp(target)
+    for b in range(3):
+        np.testing.assert_allclose(ratio[b], ratio[b].flat[0], rtol=1e-12)
+    const = np.full((2, 3, 3, 3), 0.7)
+    np.testing.assert_allclose(U.loss_weights(const, True), 1.0, rtol=1e-12)
+    assert np.array_equal(U.loss_weights(target, False), np.ones_like(target))
+    pred = target + rng.standard_normal(target.shape) * 0.1
+    e = np.exp(target)
+    by_hand = sum(float(np.sum(e[b] * (pred[b] - target[b]) ** 2) / np.sum(e[b])) for b in range(3)) / 3
+    assert U.loss(pred, target, True) == pytest.approx(by_hand, rel=1e-12)
 
 
 def test_adam_closed_form():
