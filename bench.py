@@ -470,8 +470,12 @@ def surrogate_bench(torch, args):
     net = spnn.UNet(c0, n, batch)
     net.set_params(spnn.init_params(c0, 7))
     log = []
-    losses, train_s = sg.train(net, train_set, args.surrogate_steps, batch,
-                               on_log=lambda st, l: log.append((st, l)))
+    spnn.spnn_set_option("loss_fluence_weight", 1 if args.surrogate_loss == "fluence" else 0)
+    try:
+        losses, train_s = sg.train(net, train_set, args.surrogate_steps, batch,
+                                   on_log=lambda st, l: log.append((st, l)))
+    finally:
+        spnn.spnn_set_option("loss_fluence_weight", 0)
     ev = sg.evaluate(net, test_set, batch)
     with Clocks(0) as clk:
         rate = sg.inference_rate(net, test_set, batch, reps=10)
@@ -503,7 +507,7 @@ def surrogate_bench(torch, args):
                                    f"{args.surrogate_photons:.0e} photons, {args.surrogate_test} held-out masks "
                                    f"judged against {args.surrogate_ref_photons:.0e}-photon Monte Carlo; "
                                    f"batch {batch}",
-                       "params": net.param_count},
+                       "params": net.param_count, "loss": args.surrogate_loss},
             "mc_fields_per_s": mc_rate, "speedup_vs_mc": rate["fields_per_s"] / mc_rate,
             "heldout": ev,
             "equal_time_mc": {"photons": eq_photons, "rms_w_mean": float(np.nanmean(eq_rms)),
@@ -578,6 +582,8 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=8192)
     ap.add_argument("--surrogate-test", type=int, default=128)
     ap.add_argument("--surrogate-steps", type=int, default=3000)
+    ap.add_argument("--surrogate-loss", default="mse", choices=["mse", "fluence"],
+                    help="training loss: squared log-fluence error, or the same weighted by fluence")
     ap.add_argument("--surrogate-batch", type=int, default=256)
     ap.add_argument("--surrogate-photons", type=int, default=10_000_000)
     ap.add_argument("--surrogate-ref-photons", type=int, default=100_000_000,

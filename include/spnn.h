@@ -83,6 +83,10 @@ int spnn_status(void* stream);
  *                           reports (default 2: the query has answered one CTA
  *                           per SM where two are resident), each claiming tiles
  *                           in order until none are left; 0: one CTA per tile
+ *   SPNN_OPT_LOSS_FLUENCE_WEIGHT 1: spnn_unet_backward weighs each voxel's
+ *                           squared error by exp(target) over its sample's mean
+ *                           of exp(target) (targets are log fluences); 0
+ *                           (default): unweighted
  * Settings that do not fit a layer fall back to the automatic choice.
  */
 #define SPNN_OPT_CONV_SUBTILES 1
@@ -91,6 +95,7 @@ int spnn_status(void* stream);
 #define SPNN_OPT_WGRAD_HALO 4
 #define SPNN_OPT_CONV_FULL_HALO 5
 #define SPNN_OPT_ROWS_PERSISTENT 7
+#define SPNN_OPT_LOSS_FLUENCE_WEIGHT 8
 int spnn_set_option(int key, int value);
 
 /* Elements (BF16) of a packed weight operand for a layer. */
@@ -193,8 +198,9 @@ int spnn_unet_get_grads(spnn_unet_t* net, float* grads);
 /* Forward of `batch` samples: x BF16 chunk planes [2][batch][n][n][n][8]; pred FP32 (batch, n^3). */
 int spnn_unet_forward(spnn_unet_t* net, const void* x, int batch, float* pred, void* stream);
 /*
- * Backward of the last forward (same x, same batch): loss = mean (pred -
- * target)^2 over batch * n^3 voxels, accumulated into *loss (FP64 device
+ * Backward of the last forward (same x, same batch): loss = mean w (pred -
+ * target)^2 over batch * n^3 voxels (w = 1, or the fluence weights of
+ * SPNN_OPT_LOSS_FLUENCE_WEIGHT), accumulated into *loss (FP64 device
  * scalar, caller zeroes it; may be NULL); gradients overwrite the
  * network's gradient buffer.
  */

@@ -178,7 +178,7 @@ void rows_geometry(RowsParams& p) {
 // Launch tuning (spnn_set_option): conv3 subtiles per CTA, chunk planes per
 // K-step, and the shared-memory budget of the stage ring; 0 = automatic.
 int g_opt_mt = 0, g_opt_planes = 0, g_opt_stage_kb = 0, g_opt_wgrad_halo = 1, g_opt_full_halo = 0,
-    g_opt_rows_persistent = 2;
+    g_opt_rows_persistent = 2, g_opt_loss_fluence = 0;
 
 int stage_budget() { return (g_opt_stage_kb > 0 ? g_opt_stage_kb : 110) * 1024; }
 
@@ -784,13 +784,31 @@ __global__ void phase_profile_kernel(const float* __restrict__ log_phi, const ui
     }
 }
 
-// Loss and head backward, one thread per voxel: d = pred - target,
-// loss += d^2 / n, dp = 2 d / n; g[v, c] = dp h[c] (a[v, c] > 0);
-// dh[c] += dp a[v, c]; dc += dp.
+// Fluence-weighted loss: norm[b] = voxels / sum over sample b of exp(target),
+// one block per sample (FP64 sum).
+__global__ void loss_norm_kernel(const float* __restrict__ target, long long per_sample, float* __restrict__ norm) {
+    __shared__ double part[8];
+    const float* t = target + (long long)blockIdx.x * per_sample;
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < per_sample; i += blockDim.x) acc += (double)expf(t[i]);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += part[w];
+        norm[blockIdx.x] = (float)((double)per_sample / sum);
+    }
+}
+
+// Loss and head backward, one thread per voxel: d = pred - target, weight
+// w = 1 or (norm given) exp(target) norm[sample]; loss += w d^2 / n,
+// dp = 2 w d / n; g[v, c] = dp h[c] (a[v, c] > 0); dh[c] += dp a[v, c]; dc += dp.
 template <int C>
 __global__ void loss_head_kernel(const float* __restrict__ pred, const float* __restrict__ target,
                                  const __nv_bfloat16* __restrict__ act, const float* __restrict__ hw,
-                                 long long total, double inv_n, double* loss, __nv_bfloat16* __restrict__ g,
+                                 long long total, double inv_n, const float* __restrict__ norm,
+                                 long long per_sample, double* loss, __nv_bfloat16* __restrict__ g,
                                  float* __restrict__ dhw, float* __restrict__ dhb) {
     __shared__ float sh[C + 1];
     __shared__ double sl;
@@ -804,8 +822,9 @@ __global__ void loss_head_kernel(const float* __restrict__ pred, const float* __
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const double d = (double)pred[i] - (double)target[i];
-        l += d * d;
-        const float dp = (float)(2.0 * d * inv_n);
+        const double wv = norm ? (double)(expf(target[i]) * norm[i / per_sample]) : 1.0;
+        l += wv * d * d;
+        const float dp = (float)(2.0 * wv * d * inv_n);
         acc[C] += dp;
 #pragma unroll
         for (int c0 = 0; c0 < C; c0 += 8) {
@@ -888,6 +907,7 @@ struct spnn_unet {
     std::vector<Layer> L;
     size_t nparam = 0, head_w = 0, head_b = 0;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    float* loss_norm = nullptr;      // [max_batch]: per-sample 1 / mean exp(target) (fluence-weighted loss)
     const void* last_x = nullptr;
     float* last_pred = nullptr;
     int last_batch = 0;
@@ -912,6 +932,7 @@ void free_net(spnn_unet* net) {
         cudaFree(l.grad);
     }
     cudaFree(net->params);
+    cudaFree(net->loss_norm);
     cudaFree(net->grads);
     cudaFree(net->m);
     cudaFree(net->v);
@@ -971,6 +992,10 @@ int spnn_set_option(int key, int value) {
         return SPNN_OK;
     case SPNN_OPT_CONV_FULL_HALO:
         g_opt_full_halo = value != 0;
+        return SPNN_OK;
+    case SPNN_OPT_LOSS_FLUENCE_WEIGHT:
+        if (value != 0 && value != 1) return fail(SPNN_EINVAL, "loss weighting must be 0 or 1");
+        g_opt_loss_fluence = value;
         return SPNN_OK;
     case SPNN_OPT_ROWS_PERSISTENT:
         if (value < 0 || value > 16) return fail(SPNN_EINVAL, "persistent grid multiple %d not in 0..16", value);
@@ -1075,7 +1100,8 @@ spnn_unet_t* spnn_unet_create(int c0, int n, int max_batch) {
     off += 1;
     net->nparam = off;
     bool ok = cudaMalloc(&net->params, off * 4) == cudaSuccess && cudaMalloc(&net->grads, off * 4) == cudaSuccess &&
-              cudaMalloc(&net->m, off * 4) == cudaSuccess && cudaMalloc(&net->v, off * 4) == cudaSuccess;
+              cudaMalloc(&net->m, off * 4) == cudaSuccess && cudaMalloc(&net->v, off * 4) == cudaSuccess &&
+              cudaMalloc(&net->loss_norm, (size_t)max_batch * 4) == cudaSuccess;
     for (auto& l : net->L) {
         if (!ok) break;
         const size_t pe = spnn_packed_elems(l.kind, l.cin, l.cout) * 2;
@@ -1169,17 +1195,23 @@ int spnn_unet_backward(spnn_unet_t* net, const float* target, int batch, double*
     cudaStream_t st = as_stream(stream);
     CU(cudaMemsetAsync(net->grads, 0, net->nparam * 4, st));
     auto& last = net->L[kLayers - 1];
-    const long long vox = (long long)batch * net->n * net->n * net->n;
+    const long long per_sample = (long long)net->n * net->n * net->n;
+    const long long vox = (long long)batch * per_sample;
     const double inv_n = 1.0 / (double)vox;
     const int blocks = grid_for(vox, 256);
+    const float* norm = nullptr;
+    if (g_opt_loss_fluence) {
+        loss_norm_kernel<<<batch, 256, 0, st>>>(target, per_sample, net->loss_norm);
+        norm = net->loss_norm;
+    }
     if (net->c0 == 16)
         loss_head_kernel<16><<<blocks, 256, 0, st>>>(net->last_pred, target, last.act, net->params + net->head_w,
-                                                     vox, inv_n, loss, last.grad, net->grads + net->head_w,
-                                                     net->grads + net->head_b);
+                                                     vox, inv_n, norm, per_sample, loss, last.grad,
+                                                     net->grads + net->head_w, net->grads + net->head_b);
     else
         loss_head_kernel<32><<<blocks, 256, 0, st>>>(net->last_pred, target, last.act, net->params + net->head_w,
-                                                     vox, inv_n, loss, last.grad, net->grads + net->head_w,
-                                                     net->grads + net->head_b);
+                                                     vox, inv_n, norm, per_sample, loss, last.grad,
+                                                     net->grads + net->head_w, net->grads + net->head_b);
     CU(cudaGetLastError());
     for (int i = kLayers - 1; i >= 0; --i) {
         auto& l = net->L[i];

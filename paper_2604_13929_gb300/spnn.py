@@ -139,7 +139,7 @@ def spnn_status(stream=None):
 
 
 OPT = {"conv_subtiles": 1, "conv_planes": 2, "stage_kb": 3, "wgrad_halo": 4, "conv_full_halo": 5,
-       "rows_persistent": 7}
+       "rows_persistent": 7, "loss_fluence_weight": 8}
 
 
 def spnn_set_option(key, value: int):

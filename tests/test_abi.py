@@ -124,6 +124,8 @@ def test_surrogate_options_are_validated_without_a_device(nnlib):
     assert nnlib.spnn_set_option(spnn.OPT["rows_persistent"], -1) == spnn.SPNN_EINVAL
     assert nnlib.spnn_set_option(spnn.OPT["rows_persistent"], 17) == spnn.SPNN_EINVAL
     assert nnlib.spnn_set_option(spnn.OPT["wgrad_halo"], 3) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_set_option(spnn.OPT["loss_fluence_weight"], 2) == spnn.SPNN_EINVAL
+    assert nnlib.spnn_set_option(spnn.OPT["loss_fluence_weight"], 0) == spnn.SPNN_OK
     for key in ("conv_subtiles", "conv_planes", "stage_kb", "wgrad_halo", "conv_full_halo", "rows_persistent"):
         assert nnlib.spnn_set_option(spnn.OPT[key], 0) == spnn.SPNN_OK
     assert nnlib.spnn_set_option(spnn.OPT["wgrad_halo"], 2) == spnn.SPNN_OK

@@ -323,6 +323,55 @@ def test_unet_backward_matches_oracle(S, net_run):
             assert rel < 0.03 and cos > 0.999, (name, which, rel, cos)
 
 
+def test_unet_backward_fluence_weighted_matches_oracle(S):
+    """The fluence-weighted loss (SPNN_OPT_LOSS_FLUENCE_WEIGHT): loss value and
+    parameter gradients against the oracle's weighted chain rule on the GPU's
+    own activations, same bounds as the unweighted comparison."""
+    rng = np.random.default_rng(12)
+    params = U.init_params(C0, 23)
+    net = S.UNet(C0, N, BATCH)
+    net.set_params(S.flatten_params(params, C0))
+    mask = (rng.random((BATCH, N, N, N)) < 0.7).astype(np.uint8)
+    optics = np.stack([rng.uniform(0.1, 2.0, BATCH), rng.uniform(0.001, 0.05, BATCH),
+                       rng.uniform(0.0, 0.9, BATCH)], axis=1).astype(np.float32)
+    x = zeros_act(BATCH, N, N, N, 16)
+    S.spnn_pack_input(torch.from_numpy(mask).cuda(), torch.from_numpy(optics).cuda(), x)
+    pred = torch.zeros((BATCH, N, N, N), dtype=torch.float32, device="cuda")
+    net.forward(x, pred)
+    acts = [net.activation(i, BATCH) for i in range(20)]
+    # log-fluence-like targets: a depth decay plus noise, so the weights span decades
+    z = np.arange(N, dtype=np.float64)[None, :, None, None]
+    tgt = -0.15 * z + rng.standard_normal((BATCH, N, N, N)) * 0.3
+    target = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    try:
+        S.spnn_set_option("loss_fluence_weight", 1)
+        net.backward(target, loss)
+        S.spnn_status()
+    finally:
+        S.spnn_set_option("loss_fluence_weight", 0)
+    grads = net.get_grads()
+    net.close()
+    table = U.layer_table(C0)
+    act = {"x": f64(x)}
+    for (name, *_), a in zip(table, acts):
+        act[name] = f64(a)
+    p64 = pred.cpu().numpy().astype(np.float64)
+    t64 = target.cpu().numpy().astype(np.float64)
+    P = {k: (w_bf(w) if k != "head" else w.astype(np.float32).astype(np.float64), b) for k, (w, b) in params.items()}
+    ref = U.backward(P, act, p64, t64, C0, fluence_weighted=True)
+    got = S.unflatten_params(grads, table, C0)
+    assert float(loss.item()) == pytest.approx(U.loss(p64, t64, fluence_weighted=True), rel=1e-5)
+    assert float(loss.item()) != pytest.approx(U.loss(p64, t64), rel=1e-2)
+    for name in [t[0] for t in table] + ["head"]:
+        for which in (0, 1):
+            r = np.asarray(ref[name][which], dtype=np.float64).ravel()
+            g = np.asarray(got[name][which], dtype=np.float64).ravel()
+            rel = np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-30)
+            cos = float(g @ r / max(np.linalg.norm(g) * np.linalg.norm(r), 1e-30))
+            assert rel < 0.03 and cos > 0.999, (name, which, rel, cos)
+
+
 def test_unet_adam_step(S, net_run):
     net = net_run["net"]
     p0 = net.get_params().astype(np.float64)
