@@ -115,9 +115,9 @@ def test_down_forward(S):
           what="down")
 
 
-def test_up_forward_two_column_tiles(S):
+def test_up_forward_column_tiles(S):
     rng = np.random.default_rng(4)
-    B, D, H, W, c0, co = 2, 4, 4, 8, 32, 64       # N = 8 * 64 = 512: two 256-column tiles
+    B, D, H, W, c0, co = 2, 4, 4, 8, 32, 64       # N = 8 * 64 = 512: four 128-column tiles
     x = bf(rnd(rng, (B, D, H, W, c0)))
     w = rnd(rng, (8, c0, co), 0.2)
     b = rnd(rng, co, 0.5)
