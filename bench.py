@@ -39,7 +39,7 @@ WORKLOAD = ("256^3 Cahn-Hilliard spinodal mask (dt 0.1, 4000 steps, seed 0), por
             "1e8 photons per step; FP32 transport; Q32.32 voxel fluence field")
 # Algorithmic lane-operations per unit of work: the method's own operations
 # (Sec. 2.5 transport step, interaction and photon life cycle), not the
-# compiled code's.  The same table, term by term, is in the design doc section 6:
+# compiled code's, term by term:
 #   any voxel step   26 = next face 4 (two compares, two selects), segment 1,
 #                    path cap 2, deposit 6 (multiply, quantise 2, address 2,
 #                    RED 1), path 1, crossing 9 (face parameter 1, index 2,

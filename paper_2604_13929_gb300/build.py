@@ -2,7 +2,7 @@
 
 The translation units of both libraries are compiled in parallel and linked
 into ``paper_2604_13929_gb300/_lib/`` (static CUDA runtime, so the libraries
-need only the driver at run time):
+need only the NVIDIA kernel-mode driver's libcuda at run time):
 
 * libspmc -- the voxel Monte Carlo transport (include/spmc.h);
 * libspnn -- the fluence surrogate's tensor-core kernels (include/spnn.h).
