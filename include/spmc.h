@@ -95,7 +95,7 @@ enum sp_option {
                                 takes per pass of its warp, [1, 64] (8);
                                 results do not depend on it                */
     SP_OPT_BATCH_CHUNK = 18   /* batched one-launch mode, streamlined kernel:
-                                photons per warp claim, [32, 2^24] (2048);
+                                photons per warp claim, [32, 2^24] (128);
                                 results do not depend on it                */
 };
 
@@ -244,7 +244,7 @@ size_t sp_mc_result_size(void);
  * a time).  Each problem has its own bit-packed mask, Q32.32 voxel field and
  * integer tallies, exactly as an sp_mc_create handle.  With the streamlined
  * kernel (SP_OPT_KERNEL = 1, default) every warp claims chunks of
- * SP_OPT_BATCH_CHUNK (2048) photons of one problem from a shared counter and keeps that problem's
+ * SP_OPT_BATCH_CHUNK (128) photons of one problem from a shared counter and keeps that problem's
  * tallies in shared memory until it moves on; with the generic kernel (0)
  * photons of all problems are claimed one by one, so lanes of a warp carry
  * different problems.  With the same seed and photon counts every problem's

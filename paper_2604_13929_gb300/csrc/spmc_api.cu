@@ -1036,7 +1036,9 @@ struct sp_mc_batch {
     u64 *d_next = nullptr;
     int threads = 128, blocks_per_sm = 0, compact_k = 8, use_graph = 1, mode = 0;
     int variant = 1, steps_per_pass = 8;   // one-launch kernel and its steps per pass
-    u32 chunk = 2048;                      // photons per warp claim (streamlined kernel)
+    u32 chunk = 128;                       // photons per warp claim (streamlined kernel): small
+                                           // claims keep the problems in flight, and so the
+                                           // voxel fields written, few (L2)
     u64 total_chunks = 0;
     bool any_mirror = false;
     bool table_valid = false;              // device table matches table[]

@@ -82,8 +82,8 @@ def test_batch_equals_separate_runs(spmc, problems, graph, mode, kernel):
 
 @pytest.mark.parametrize("steps_per_pass,threads,chunk", [(8, 128, 2048), (3, 256, 32), (16, 64, 9000)])
 def test_one_launch_batch_is_independent_of_launch_shape(spmc, problems, steps_per_pass, threads, chunk):
-    """Chunks of photons per warp claim (2048 by default, down to one photon
-    per lane, and uneven sizes): problems far larger than one chunk, warps
+    """Chunks of photons per warp claim (128 by default; 2048, one photon per
+    lane, and an uneven size here): problems far larger than one chunk, warps
     changing problem many times, any launch shape."""
     n = [70000, 9000, 3000, 41000]
     with spmc.Batch(problems, graph=0, batch_mode=0, steps_per_pass=steps_per_pass, threads=threads,
