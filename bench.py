@@ -261,6 +261,21 @@ def batch_bench(args, torch, dist, spmc, world, rank, local_rank, barrier):
     t0 = time.perf_counter()
     problems = inputs.batch_workload(64, device="cuda")
     gen_s = time.perf_counter() - t0
+    if args.profile_launch:
+        # profiling case: the one-launch mode at its default shape, no graph, no
+        # autotuning; one warm-up launch of N/10 photons per problem, then one of N
+        n = args.profile_launch
+        with spmc.Batch(problems, graph=0, batch_mode=0) as pb:
+            pb.run([max(n // 10, 1)] * len(problems), SEED + 1, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.run([n] * len(problems), SEED, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            steps = sum(pb.tallies(i, stream)["steps"] for i in range(len(problems)))
+        print(json.dumps({"profile_launch_photons_per_problem": n, "problems": len(problems),
+                          "ms": e0.elapsed_time(e1), "steps": steps}), flush=True)
+        return
     n_each = 10_000_000
     b = spmc.Batch(problems)
     # the autotuner times each candidate on a tenth of a step: large enough that
@@ -594,7 +609,8 @@ def main():
                     help="with --surrogate-profile: no warm-up step")
     ap.add_argument("--profile-launch", type=int, default=0, metavar="N",
                     help="profiling case: one warm-up launch of N/10 photons, then one timed "
-                         "launch of N photons on the workload; prints its time and exits")
+                         "launch of N photons on the workload (per problem with --workload "
+                         "batch); prints its time and exits")
     args = ap.parse_args()
 
     rank = _env_int("RANK", 0)
