@@ -62,15 +62,15 @@ SFU_INTERACT, SFU_PHOTON = 10, 1
 ISSUE_PER_SM_CLK = 4          # warp instructions per SM per clock (4 schedulers)
 SFU_PER_SM_CLK = 16           # XU lane-operations per SM per clock
 # DRAM bytes (read + write) per photon of the transport kernel from one ncu capture
-# (a 2e6-photon launch of this workload: 3.592e9 B read + 2.897e10 B written),
+# (a 2e6-photon launch of this workload: 3.593e9 B read + 2.897e10 B written),
 # valid only for the kernel source it was taken on.
-TRAFFIC_CAPTURE = {"kernel_sha256_prefix": "0f1cddb9ec47f5bd", "dram_bytes_per_photon": 16281.5,
+TRAFFIC_CAPTURE = {"kernel_sha256_prefix": "3e0680a07320195d", "dram_bytes_per_photon": 16283.4,
                    "source": "profiles/transport_kernel_256cubed_phi090.md"}
 # Hardware fractions of peak of the transport kernel from the same ncu capture
 # (smsp__issue_active, sm__inst_executed_pipe_xu, lts__d_atomic_input_cycles_active),
 # reported only while the kernel source matches the capture.
-NCU_FRACTIONS = {"kernel_sha256_prefix": "0f1cddb9ec47f5bd", "issue_slots": 0.5817,
-                 "sfu_xu_pipe": 0.0164, "l2_atomic_unit": 0.1915, "warps_active": 0.3668,
+NCU_FRACTIONS = {"kernel_sha256_prefix": "3e0680a07320195d", "issue_slots": 0.5831,
+                 "sfu_xu_pipe": 0.0164, "l2_atomic_unit": 0.1924, "warps_active": 0.3668,
                  "l2_red_hit_rate": 0.6543, "registers_per_thread": 72,
                  "source": "profiles/transport_kernel_256cubed_phi090.md"}
 

@@ -437,7 +437,11 @@ transport_f32_kernel(const TransportParams p, const BatchParams bp) {
             n_solid += (seg > 0.0f && !pore) ? 1u : 0u;
             const u64 q = q32_bits(dep);
             if constexpr (kField) {
-                if (q) atomicAdd(field + (((u64)brick << 6) | bit), q);
+                if constexpr (kBatch) {   // field pointer from the problem table: say it is global
+                    if (q) red_add_global(field + (((u64)brick << 6) | bit), q);
+                } else {
+                    if (q) atomicAdd(field + (((u64)brick << 6) | bit), q);
+                }
             } else {
                 if (pore) acc_p += q; else acc_s += q;
             }
