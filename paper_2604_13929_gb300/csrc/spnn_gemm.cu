@@ -117,10 +117,11 @@ __device__ __forceinline__ void issue_conv_step(int mt, int eh, uint32_t tmem, u
 // B tile: kc_step planes of n_tile rows x 16 bytes, K-major.
 //
 // Persistent, dynamically scheduled: the producer claims the next tile from a
-// global counter (so the tiles in flight stay a compact window of the grid,
-// and the halo rows that neighbouring tiles share stay in L2) and hands its
-// index to the MMA and epilogue warps through a ring of four shared slots
-// (tile_full / tile_empty; index -1 ends the CTA).  The stage ring runs on
+// global counter (so any grid size is safe: a CTA that becomes resident only
+// after the others have claimed every tile finds none and exits; tiles are
+// claimed in grid order) and hands its index to the MMA and epilogue warps
+// through a ring of four shared slots (tile_full / tile_empty; index -1 ends
+// the CTA).  The stage ring runs on
 // across tiles, so the next tile's operands load while the current one
 // multiplies.  The accumulators of consecutive tiles alternate
 // between two TMEM buffers (nbuf = 2 when they fit in 512 columns): the
